@@ -1,0 +1,228 @@
+/*
+ * fsi.h -- C ABI of the GB300 monolithic fluid-structure Newton-Krylov-Schwarz solver.
+ *
+ * The solver advances the monolithically coupled ALE fluid-structure system of
+ * Kong, Kheyfets, Finol & Cai (arXiv 1810.04289) by one backward-Euler step per
+ * fsi_step call:
+ *   - ALE map x = X + d_m and harmonic mesh motion (Sec. 2.1, Eq. 1);
+ *   - St. Venant-Kirchhoff wall, total Lagrangian (Sec. 2.1, Eq. 2);
+ *   - incompressible Navier-Stokes on the moving fluid domain (Sec. 2.1, Eq. 3),
+ *     stabilised P1-P1 (Sec. 2.2), strong interface coupling with one set of
+ *     unknowns per interface node (Sec. 2.2, Eq. 6-7);
+ *   - backward Euler in time, F(y) = 0 per step (Sec. 2.2, Eq. 9-10);
+ *   - inexact Newton with backtracking (Sec. 3, Eq. 11-12), right-preconditioned
+ *     GMRES with a restricted additive Schwarz preconditioner whose subdomain
+ *     solver is a block incomplete LU factorisation, ILU(k) with level of fill
+ *     k = 0..3 (Sec. 3, Eq. 13-16; Sec. 4.3).
+ *
+ * Unknowns: 7 per mesh node, node-major: y[i*7 + c], c = 0..6 =
+ * [u_x, u_y, u_z, p, d_x, d_y, d_z] (fluid velocity, pressure, displacement; on
+ * wall-only nodes the u and p slots are constrained to zero). Units: cm, g, s.
+ *
+ * Conventions shared by every call:
+ *   - Nothing throws across the ABI. Every call returns an fsi_status;
+ *     fsi_last_error() gives a message for the last failure on that context.
+ *   - Pointers documented as "device" must be CUDA device (or managed) memory
+ *     of the current device; pointers documented as "host" are host memory.
+ *     The caller owns every pointer it passes; the context keeps none of them
+ *     beyond the call (mesh arrays are copied by fsi_create).
+ *   - All GPU work of a context is ordered on the CUDA stream given to
+ *     fsi_create (NULL = the legacy default stream). Calls return after the
+ *     work they need to report a result is complete on that stream.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef FSI_GB300_H
+#define FSI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsi_ctx fsi_ctx;
+
+typedef enum {
+  FSI_OK = 0,
+  FSI_ERR_ARG = 1,              /* invalid argument (null pointer, size, option) */
+  FSI_ERR_MESH = 2,             /* invalid mesh (index out of range, degenerate tet) */
+  FSI_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+  FSI_ERR_NOMEM = 4,            /* device or host allocation failed */
+  FSI_ERR_ZERO_PIVOT = 5,       /* singular 7x7 pivot block in the ILU factorisation */
+  FSI_ERR_LINEAR_DIVERGED = 6,  /* GMRES reached its iteration limit above tolerance */
+  FSI_ERR_DIVERGED = 7,         /* Newton reached its iteration limit above tolerance */
+  FSI_ERR_LINESEARCH = 8,       /* backtracking found no sufficient decrease */
+  FSI_ERR_TIMEOUT = 9,          /* a bounded device-side wait gave up */
+  FSI_ERR_NONFINITE = 10        /* NaN or Inf in the residual */
+} fsi_status;
+
+/* Node tag bits (fsi_mesh.node_tag). FLUID: belongs to a fluid tet; WALL: to a
+ * wall tet; INTERFACE: vertex of the wet interface (a fluid-tet face shared with
+ * a wall tet, Sec. 4.8, Algorithm 1); INLET / OUTLET: fluid node on an inflow /
+ * outflow cap; WALL_END: wall node on a cap (clamped, Eq. 2); OUTER: outer wall
+ * surface (zero traction). */
+enum {
+  FSI_TAG_FLUID = 1, FSI_TAG_WALL = 2, FSI_TAG_INTERFACE = 4, FSI_TAG_INLET = 8,
+  FSI_TAG_OUTLET = 16, FSI_TAG_WALL_END = 32, FSI_TAG_OUTER = 64
+};
+
+/* The mesh: host arrays, copied at fsi_create.
+ *   X            [n_nodes*3]  reference coordinates (cm), node-major
+ *   tets         [n_tets*4]   vertex ids, positively oriented
+ *   tet_domain   [n_tets]     0 = fluid (lumen), 1 = wall
+ *   node_tag     [n_nodes]    FSI_TAG_* bits
+ *   node_problem [n_nodes]    problem id of each node for batched meshes of
+ *                             independent vessels, or NULL for one problem */
+typedef struct {
+  int64_t n_nodes, n_tets;
+  const double *X;
+  const int32_t *tets;
+  const uint8_t *tet_domain;
+  const uint32_t *node_tag;
+  const int32_t *node_problem;
+} fsi_mesh;
+
+/* Materials (Sec. 2.1): blood density rho_f (g/cm^3) and dynamic viscosity
+ * mu_f (P); wall density rho_s, Young's modulus E_s (dyn/cm^2), Poisson ratio
+ * nu_s, damping eta_s (g/(cm^3 s)). */
+typedef struct {
+  double rho_f, mu_f, rho_s, E_s, nu_s, eta_s;
+} fsi_material;
+
+/* Inflow boundary of one problem (Eq. 3, u_f = v_f^d on the inlet):
+ * u = U(t) (1 - r^2/R^2)_+ n, U(t) = peak (1 + amp sin(2 pi freq t + phase)),
+ * r = distance from the line through `center` along `normal` (the unit normal
+ * pointing into the lumen), R = radius. rigid_wall != 0 clamps every wall node
+ * (d = 0), which reduces the problem to flow in a rigid vessel. */
+typedef struct {
+  double center[3], normal[3], radius;
+  double peak, amp, freq, phase;
+  int32_t rigid_wall;
+} fsi_bc;
+
+/* Solver options (Sec. 4: defaults Newton rtol 1e-6, GMRES rtol 1e-3,
+ * overlap 1). precision 0 = FP64 throughout; 1 = mixed: Jacobian, ILU factors,
+ * preconditioner apply and matrix values in FP32, residual, Krylov basis,
+ * Arnoldi, least squares and Newton update in FP64. Start from
+ * fsi_default_options. In fsi_create, zero or negative dt, tolerances, iteration
+ * counts, restart and n_subdomains, and negative overlap / ilu_level, take the
+ * defaults; precision, jac_lag (>= 1), ilu_level and overlap are used as given. */
+typedef struct {
+  double dt;              /* time step (s) */
+  double newton_rtol;     /* stop when ||F|| <= newton_rtol ||F(y^(0))|| */
+  double newton_atol;     /* or when ||F|| <= newton_atol */
+  double gmres_rtol;      /* GMRES stop: ||J dy + F|| <= gmres_rtol ||F|| */
+  int32_t newton_maxit;
+  int32_t gmres_restart;  /* Krylov dimension per cycle (<= 64) */
+  int32_t gmres_maxit;    /* total GMRES iterations per linear solve */
+  int32_t n_subdomains;   /* Schwarz subdomains (Sec. 3) */
+  int32_t overlap;        /* overlap delta in node layers (Sec. 3) */
+  int32_t precision;      /* 0 FP64, 1 mixed FP32/FP64 */
+  int32_t jac_lag;        /* reuse the Jacobian for this many Newton iterations (Eq. 12), >= 1 */
+  int32_t ilu_level;      /* level of fill k of the subdomain block ILU(k), 0..3 (Sec. 4.3) */
+  int32_t threads_per_row;/* BSR SpMV rows-to-threads mapping: 0 = auto */
+  int32_t verbose;        /* print per-iteration norms to stderr */
+} fsi_options;
+
+typedef struct {
+  int32_t iterations;     /* GMRES iterations */
+  int32_t converged;      /* 1 if the tolerance was met */
+  double rnorm0, rnorm;   /* initial and final true residual norms ||b - J x|| */
+} fsi_solve_stats;
+
+typedef struct {
+  int32_t newton_iterations;
+  int32_t linear_iterations;   /* total GMRES iterations over the step */
+  int32_t jacobian_evaluations;
+  int32_t residual_evaluations;
+  int32_t converged;
+  double fnorm0, fnorm;        /* ||F|| at the first and last Newton iterate */
+  /* device time per phase (ms), in the paper's timing categories (Table 7) */
+  double t_funceval, t_jaceval, t_pcsetup, t_pcapply, t_spmv, t_orth, t_total;
+} fsi_step_stats;
+
+typedef struct {
+  int64_t n_nodes, n_tets, n_unknowns, nnzb;
+  int64_t n_fluid_tets, n_wall_tets;
+  int32_t n_problems, n_subdomains;
+  int64_t factor_blocks;       /* 7x7 blocks held by all subdomain factors */
+  int32_t max_levels;          /* deepest level schedule over the subdomains */
+  int64_t device_bytes;        /* device memory held by the context */
+} fsi_info;
+
+/* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,
+ * newton_maxit 20, gmres_restart 30, gmres_maxit 1000, n_subdomains 64,
+ * overlap 1, precision 0, jac_lag 1, ilu_level 1 (the paper's default subdomain
+ * solver, Sec. 4), threads_per_row 0. A negative ilu_level or overlap in the
+ * caller's options also selects the default. */
+void fsi_default_options(fsi_options *opts);
+
+/* Build a solver context for `mesh`. bc: array of n_problems inflow boundaries
+ * (n_problems >= 1; node_problem picks one per node). Performs all symbolic
+ * work on the host (block-sparse pattern, assembly gather lists, subdomain
+ * partition, overlap, RCM ordering, ILU pattern, level schedules), copies the
+ * mesh to the device and allocates every device buffer the solver needs. The
+ * state is zero until fsi_set_state. `cuda_stream` is a cudaStream_t.
+ * Errors: FSI_ERR_ARG, FSI_ERR_MESH, FSI_ERR_NOMEM, FSI_ERR_CUDA; *out is NULL
+ * on failure. */
+fsi_status fsi_create(const fsi_mesh *mesh, const fsi_material *mat, const fsi_bc *bc,
+                      int32_t n_problems, const fsi_options *opts, void *cuda_stream,
+                      fsi_ctx **out);
+
+/* Release every device and host resource of the context. NULL is accepted. */
+fsi_status fsi_destroy(fsi_ctx *ctx);
+
+/* Set the time level: y_n (the last accepted state), y_{n-1}, y_{n-2} and the
+ * time t_n. Device pointers, [n_nodes*7] FP64 each. y_nm1 / y_nm2 may be NULL
+ * (taken equal to y_n). The next fsi_step solves for t_n + dt. */
+fsi_status fsi_set_state(fsi_ctx *ctx, const double *y_n, const double *y_nm1,
+                         const double *y_nm2, double t);
+
+/* Copy the current state y_n (device, [n_nodes*7]) and time; either may be NULL. */
+fsi_status fsi_get_state(fsi_ctx *ctx, double *y_n, double *t);
+
+/* F(y) for the step that ends at t_n + dt, with y_{n-1}, y_{n-2} taken from
+ * the context state (Eq. 9-10). y, F: device, [n_nodes*7] FP64. Constraint
+ * rows (Dirichlet caps, inlet profile, kinematic interface rows, the unused u/p
+ * slots of wall-only nodes) hold (value - prescribed). */
+fsi_status fsi_residual(fsi_ctx *ctx, const double *y, double *F);
+
+/* Assemble the exact Jacobian J = dF/dy at y (device, [n_nodes*7]) into the
+ * context's block-sparse (7x7 BSR) matrix, in FP64 or, in mixed precision, in
+ * FP32. Marks the preconditioner stale; it is rebuilt by the next linear solve. */
+fsi_status fsi_jacobian(fsi_ctx *ctx, const double *y);
+
+/* Copy the assembled Jacobian out. Host pointers, any may be NULL:
+ * row_ptr [n_nodes+1], col [nnzb] (sorted block columns), vals [nnzb*49]
+ * (row-major 7x7 blocks, converted to FP64). */
+fsi_status fsi_jacobian_export(fsi_ctx *ctx, int32_t *row_ptr, int32_t *col, double *vals);
+
+/* y = J x with the assembled Jacobian. Device pointers, [n_nodes*7] FP64. */
+fsi_status fsi_spmv(fsi_ctx *ctx, const double *x, double *y);
+
+/* z = B^{-1} r, the restricted additive Schwarz preconditioner of Eq. 16 built
+ * from the assembled Jacobian (built first if stale). Device pointers, FP64. */
+fsi_status fsi_pc_apply(fsi_ctx *ctx, const double *r, double *z);
+
+/* Solve J x = rhs with right-preconditioned restarted GMRES to the context's
+ * gmres_rtol on the true residual. Device pointers, [n_nodes*7]; x is the
+ * output (initial guess 0). stats may be NULL. Returns
+ * FSI_ERR_LINEAR_DIVERGED (x still holds the last iterate) if gmres_maxit is
+ * reached. */
+fsi_status fsi_linear_solve(fsi_ctx *ctx, const double *rhs, double *x, fsi_solve_stats *stats);
+
+/* One backward-Euler step: Newton from y^(0) = y_n to the Newton tolerance,
+ * then shift the time levels (y_{n-2} <- y_{n-1} <- y_n <- y, t <- t + dt). On
+ * failure the state is left at the previous time level. stats may be NULL. */
+fsi_status fsi_step(fsi_ctx *ctx, fsi_step_stats *stats);
+
+fsi_status fsi_get_info(const fsi_ctx *ctx, fsi_info *info);
+
+/* Message of the last failure on the context (static string if ctx is NULL). */
+const char *fsi_last_error(const fsi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSI_GB300_H */

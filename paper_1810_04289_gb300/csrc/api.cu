@@ -1,0 +1,784 @@
+// C ABI of the solver (include/fsi.h): context construction, residual,
+// Jacobian, preconditioner, GMRES and the Newton step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fsi.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+using namespace fsi;
+
+namespace {
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) throw CudaError{e_, #call};  \
+  } while (0)
+
+struct StatusError {
+  fsi_status st;
+  std::string msg;
+};
+
+}  // namespace
+
+struct fsi_ctx {
+  cudaStream_t s = nullptr;
+  fsi_options opt{};
+  fsi_material mat{};
+  MatConst mc{};
+  int64_t N = 0, T = 0, Tf = 0, nnzb = 0, nunk = 0, n = 0;  // n = 7N
+  int32_t nprob = 1;
+  std::vector<void*> allocs;
+  int64_t dev_bytes = 0;
+  std::string err;
+
+  // mesh
+  double* X = nullptr;
+  int32_t* tets = nullptr;
+  uint32_t* nflag = nullptr;
+  int32_t* nprobid = nullptr;
+  double* inlet = nullptr;
+  MeshDev mesh{};
+  // assembly
+  int64_t *nptr = nullptr, *bptr = nullptr;
+  int32_t *nsrc = nullptr, *bsrc = nullptr;
+  double* Fe = nullptr;
+  void* Ke = nullptr;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  int32_t* diag = nullptr;
+  void* vals = nullptr;
+  bool mixed = false;
+  bool have_jac = false;
+  // state
+  double *yn = nullptr, *ynm1 = nullptr, *ynm2 = nullptr;
+  double t = 0.0;
+  // Newton
+  double *yk = nullptr, *ytr = nullptr, *F = nullptr, *Ft = nullptr, *dy = nullptr, *rhs = nullptr;
+  // GMRES
+  int32_t m = 30;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *ylsq = nullptr;
+  double *hA = nullptr, *hB = nullptr, *partial = nullptr, *scal = nullptr, *r = nullptr;
+  double* hbuf = nullptr;  // pinned host scalars
+  // RAS
+  RasPlan plan;
+  RasDev ras{};
+  void* fac = nullptr;
+  void* work = nullptr;
+  int32_t* errflag = nullptr;
+  bool pc_stale = true;
+  // timing
+  std::vector<cudaEvent_t> evpool;
+  size_t evused = 0;
+  struct Span {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> spans;
+  double phase_ms[8] = {0};
+  bool timing = false;
+
+  template <class U>
+  U* dalloc(int64_t count) {
+    void* p = nullptr;
+    const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(U);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) throw StatusError{FSI_ERR_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)};
+    allocs.push_back(p);
+    dev_bytes += (int64_t)bytes;
+    return (U*)p;
+  }
+  template <class U>
+  U* upload(const std::vector<U>& v) {
+    U* p = dalloc<U>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+
+  cudaEvent_t ev() {
+    if (evused == evpool.size()) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      evpool.push_back(e);
+    }
+    return evpool[evused++];
+  }
+  int begin_phase() {
+    if (!timing) return -1;
+    cudaEvent_t a = ev();
+    CK(cudaEventRecord(a, s));
+    spans.push_back({0, a, nullptr});
+    return (int)spans.size() - 1;
+  }
+  void end_phase(int h, int phase) {
+    if (h < 0) return;
+    cudaEvent_t b = ev();
+    CK(cudaEventRecord(b, s));
+    spans[h].phase = phase;
+    spans[h].b = b;
+  }
+  void resolve_phases() {
+    if (!timing) return;
+    CK(cudaStreamSynchronize(s));
+    for (auto& sp : spans) {
+      float ms = 0;
+      if (sp.b) CK(cudaEventElapsedTime(&ms, sp.a, sp.b));
+      phase_ms[sp.phase] += ms;
+    }
+    spans.clear();
+    evused = 0;
+  }
+};
+
+enum { PH_FUNC = 0, PH_JAC, PH_PCSETUP, PH_PCAPPLY, PH_SPMV, PH_ORTH };
+
+namespace {
+
+fsi_status fail(fsi_ctx* c, fsi_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+template <class Fn>
+fsi_status guarded(fsi_ctx* c, Fn&& fn) {
+  try {
+    return fn();
+  } catch (const CudaError& e) {
+    return fail(c, FSI_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+  } catch (const StatusError& e) {
+    return fail(c, e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, FSI_ERR_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, FSI_ERR_MESH, e.what());
+  }
+}
+
+double read_scalar(fsi_ctx* c, const double* dptr) {
+  CK(cudaMemcpyAsync(c->hbuf, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return c->hbuf[0];
+}
+
+void check_launch() { CK(cudaGetLastError()); }
+
+// ---- F(y) for the step ending at t_n + dt (previous levels y_n, y_{n-1})
+void residual(fsi_ctx* c, const double* y, double* F) {
+  int h = c->begin_phase();
+  launch_elem_residual(c->mesh, c->mc, y, c->yn, c->ynm1, c->Fe, c->s);
+  launch_gather_residual(c->mesh, c->nptr, c->nsrc, c->Fe, F, c->s);
+  launch_constraint_residual(c->mesh, c->mc, c->t + c->opt.dt, y, c->yn, F, c->s);
+  check_launch();
+  c->end_phase(h, PH_FUNC);
+}
+
+double norm(fsi_ctx* c, const double* x) {
+  launch_norm(c->n, x, c->partial, c->scal, c->s);
+  return read_scalar(c, c->scal);
+}
+
+void jacobian(fsi_ctx* c, const double* y) {
+  int h = c->begin_phase();
+  if (c->mixed) {
+    launch_elem_jacobian<float>(c->mesh, c->mc, y, c->yn, c->ynm1, (float*)c->Ke, c->s);
+    launch_gather_jacobian<float>(c->nnzb, c->bptr, c->bsrc, (const float*)c->Ke, (float*)c->vals, c->s);
+    launch_constraint_jacobian<float>(c->mesh, c->mc, c->diag, (float*)c->vals, c->s);
+  } else {
+    launch_elem_jacobian<double>(c->mesh, c->mc, y, c->yn, c->ynm1, (double*)c->Ke, c->s);
+    launch_gather_jacobian<double>(c->nnzb, c->bptr, c->bsrc, (const double*)c->Ke, (double*)c->vals, c->s);
+    launch_constraint_jacobian<double>(c->mesh, c->mc, c->diag, (double*)c->vals, c->s);
+  }
+  check_launch();
+  c->end_phase(h, PH_JAC);
+  c->have_jac = true;
+  c->pc_stale = true;
+}
+
+void spmv(fsi_ctx* c, const double* x, double* y) {
+  int h = c->begin_phase();
+  if (c->mixed)
+    launch_bsr_spmv<float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x, y, c->s);
+  else
+    launch_bsr_spmv<double>(c->N, c->row_ptr, c->col, (const double*)c->vals, x, y, c->s);
+  check_launch();
+  c->end_phase(h, PH_SPMV);
+}
+
+void pc_setup(fsi_ctx* c) {
+  int h = c->begin_phase();
+  CK(cudaMemsetAsync(c->errflag, 0, sizeof(int32_t), c->s));
+  if (c->mixed) {
+    launch_ras_extract<float, float>(c->ras, (const float*)c->vals, (float*)c->fac, c->s);
+    launch_ras_factor<float>(c->ras, (float*)c->fac, c->errflag, c->s);
+  } else {
+    launch_ras_extract<double, double>(c->ras, (const double*)c->vals, (double*)c->fac, c->s);
+    launch_ras_factor<double>(c->ras, (double*)c->fac, c->errflag, c->s);
+  }
+  check_launch();
+  c->end_phase(h, PH_PCSETUP);
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&c->hbuf[1], c->errflag, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  std::memcpy(&e, &c->hbuf[1], sizeof(int32_t));
+  if (e) throw StatusError{FSI_ERR_ZERO_PIVOT, "singular pivot block in the subdomain ILU factorisation"};
+  c->pc_stale = false;
+}
+
+void pc_apply(fsi_ctx* c, const double* rin, double* z) {
+  int h = c->begin_phase();
+  if (c->mixed)
+    launch_ras_apply<float>(c->ras, (const float*)c->fac, rin, (float*)c->work, z, c->s);
+  else
+    launch_ras_apply<double>(c->ras, (const double*)c->fac, rin, (double*)c->work, z, c->s);
+  check_launch();
+  c->end_phase(h, PH_PCAPPLY);
+}
+
+// Right-preconditioned restarted flexible GMRES (FGMRES form: the preconditioned
+// directions Z are stored, so an FP32 preconditioner is allowed), classical
+// Gram-Schmidt applied twice, Givens rotations; stops on the true residual.
+fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
+  if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
+  if (c->pc_stale) pc_setup(c);
+  const int64_t n = c->n;
+  const int32_t m = c->m, ldh = m + 1;
+  launch_fill(n, 0.0, x, c->s);
+  launch_copy(n, b, c->r, c->s);
+  double beta = norm(c, c->r);
+  const double rnorm0 = beta;
+  const double target = c->opt.gmres_rtol * beta;
+  int32_t it = 0;
+  bool conv = beta <= target || beta == 0.0;
+  while (!conv && it < c->opt.gmres_maxit) {
+    // V_0 = r / beta ; g = beta e_1
+    launch_scale_inv(n, c->r, c->scal, c->V, c->s);
+    launch_fill(ldh, 0.0, c->g, c->s);
+    launch_copy(1, c->scal, c->g, c->s);
+    int32_t k = 0;
+    for (int32_t j = 0; j < m && it < c->opt.gmres_maxit; ++j) {
+      double* vj = c->V + (int64_t)j * n;
+      double* zj = c->Z + (int64_t)j * n;
+      double* w = c->V + (int64_t)(j + 1) * n;
+      pc_apply(c, vj, zj);
+      spmv(c, zj, w);
+      int h = c->begin_phase();
+      double* Hj = c->H + (int64_t)j * ldh;
+      launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hA, c->s);
+      launch_maxpy(n, j + 1, c->V, n, c->hA, w, c->s);
+      launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hB, c->s);
+      launch_maxpy(n, j + 1, c->V, n, c->hB, w, c->s);
+      launch_add_small(j + 1, c->hA, c->hB, Hj, c->s);
+      launch_norm(n, w, c->partial, Hj + j + 1, c->s);
+      launch_scale_inv(n, w, Hj + j + 1, w, c->s);
+      launch_givens(c->H, ldh, j, c->cs, c->sn, c->g, c->scal, c->s);
+      check_launch();
+      c->end_phase(h, PH_ORTH);
+      const double res = read_scalar(c, c->scal);
+      ++it;
+      k = j + 1;
+      if (c->opt.verbose) std::fprintf(stderr, "    gmres %d: %.3e (target %.3e)\n", it, res, target);
+      if (!(res > target)) break;
+    }
+    // x += Z y
+    launch_lsq(c->H, ldh, k, c->g, c->ylsq, c->s);
+    for (int32_t q = 0; q < k; ++q) {
+      // y_q is on the device: x += y_q Z_q
+      launch_axpy_dev(n, c->ylsq + q, c->Z + (int64_t)q * n, x, c->s);
+    }
+    // true residual r = b - J x
+    spmv(c, x, c->r);
+    launch_axpby(n, 1.0, b, -1.0, c->r, c->r, c->s);
+    beta = norm(c, c->r);
+    conv = beta <= target;
+  }
+  if (st) {
+    st->iterations = it;
+    st->converged = conv ? 1 : 0;
+    st->rnorm0 = rnorm0;
+    st->rnorm = beta;
+  }
+  return conv ? FSI_OK : FSI_ERR_LINEAR_DIVERGED;
+}
+
+void fill_defaults(fsi_options* o) {
+  o->dt = 1e-3;
+  o->newton_rtol = 1e-6;
+  o->newton_atol = 1e-10;
+  o->gmres_rtol = 1e-3;
+  o->newton_maxit = 20;
+  o->gmres_restart = 30;
+  o->gmres_maxit = 1000;
+  o->n_subdomains = 64;
+  o->overlap = 1;
+  o->precision = 0;
+  o->jac_lag = 1;
+  o->ilu_level = 1;
+  o->threads_per_row = 0;
+  o->verbose = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fsi_default_options(fsi_options* o) {
+  if (o) fill_defaults(o);
+}
+
+fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_bc* bc, int32_t n_problems,
+                      const fsi_options* opts, void* cuda_stream, fsi_ctx** out) {
+  if (out) *out = nullptr;
+  if (!mesh || !mat || !bc || !out || n_problems < 1 || !mesh->X || !mesh->tets || !mesh->tet_domain ||
+      !mesh->node_tag || mesh->n_nodes <= 0 || mesh->n_tets <= 0)
+    return FSI_ERR_ARG;
+  if (mesh->n_nodes >= (int64_t)INT32_MAX || mesh->n_tets * 16 >= (int64_t)INT32_MAX) return FSI_ERR_ARG;
+  std::unique_ptr<fsi_ctx> c(new (std::nothrow) fsi_ctx());
+  if (!c) return FSI_ERR_NOMEM;
+  fsi_ctx* cp = c.get();
+  fsi_status st = guarded(cp, [&]() -> fsi_status {
+    fsi_options o;
+    fill_defaults(&o);
+    if (opts) {
+      const fsi_options& q = *opts;
+      if (q.dt > 0) o.dt = q.dt;
+      if (q.newton_rtol > 0) o.newton_rtol = q.newton_rtol;
+      if (q.newton_atol > 0) o.newton_atol = q.newton_atol;
+      if (q.gmres_rtol > 0) o.gmres_rtol = q.gmres_rtol;
+      if (q.newton_maxit > 0) o.newton_maxit = q.newton_maxit;
+      if (q.gmres_restart > 0) o.gmres_restart = q.gmres_restart;
+      if (q.gmres_maxit > 0) o.gmres_maxit = q.gmres_maxit;
+      if (q.n_subdomains > 0) o.n_subdomains = q.n_subdomains;
+      if (q.overlap >= 0) o.overlap = q.overlap;
+      o.precision = q.precision;
+      if (q.jac_lag > 0) o.jac_lag = q.jac_lag;
+      if (q.ilu_level >= 0) o.ilu_level = q.ilu_level;
+      o.threads_per_row = q.threads_per_row;
+      o.verbose = q.verbose;
+    }
+    if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
+    if (o.ilu_level < 0 || o.ilu_level > 3) throw StatusError{FSI_ERR_ARG, "ilu_level must be 0..3"};
+    if (o.gmres_restart > 64) throw StatusError{FSI_ERR_ARG, "gmres_restart must be <= 64"};
+    cp->opt = o;
+    cp->mat = *mat;
+    cp->s = (cudaStream_t)cuda_stream;
+    cp->mixed = o.precision == 1;
+    cp->m = o.gmres_restart;
+    cp->nprob = n_problems;
+    const double mu_s = mat->E_s / (2.0 * (1.0 + mat->nu_s));
+    const double lam_s = mat->E_s * mat->nu_s / ((1.0 + mat->nu_s) * (1.0 - 2.0 * mat->nu_s));
+    cp->mc = MatConst{mat->rho_f, mat->mu_f, mat->rho_s, mat->eta_s, lam_s, mu_s, o.dt};
+
+    const int64_t N = mesh->n_nodes, T0 = mesh->n_tets;
+    // validate, then order tets fluid first
+    std::vector<int32_t> tets;
+    tets.reserve(4 * T0);
+    int64_t Tf = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int64_t t = 0; t < T0; ++t) {
+        const uint8_t d = mesh->tet_domain[t];
+        if (d > 1) throw StatusError{FSI_ERR_MESH, "tet_domain must be 0 or 1"};
+        if (d != pass) continue;
+        for (int a = 0; a < 4; ++a) {
+          const int32_t v = mesh->tets[4 * t + a];
+          if (v < 0 || v >= N) throw StatusError{FSI_ERR_MESH, "tet vertex index out of range"};
+          tets.push_back(v);
+        }
+        if (pass == 0) ++Tf;
+      }
+    // positive orientation check (reference configuration)
+    for (int64_t t = 0; t < T0; ++t) {
+      const double* x0 = mesh->X + 3 * (int64_t)tets[4 * t];
+      double e[3][3];
+      for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 3; ++i) e[k][i] = mesh->X[3 * (int64_t)tets[4 * t + k + 1] + i] - x0[i];
+      const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                         e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                         e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+      if (!(det > 0)) throw StatusError{FSI_ERR_MESH, "degenerate or negatively oriented tet"};
+    }
+    // node flags: constraint rows and row routing
+    std::vector<uint32_t> flag(N, 0);
+    std::vector<int32_t> prob(N, 0);
+    int64_t nfluid = 0;
+    for (int64_t i = 0; i < N; ++i) {
+      const uint32_t tg = mesh->node_tag[i];
+      const int32_t p = mesh->node_problem ? mesh->node_problem[i] : 0;
+      if (p < 0 || p >= n_problems) throw StatusError{FSI_ERR_MESH, "node_problem out of range"};
+      prob[i] = p;
+      const bool fl = tg & FSI_TAG_FLUID, wl = tg & FSI_TAG_WALL, itf = tg & FSI_TAG_INTERFACE;
+      uint32_t f = 0;
+      if (fl) f |= NF_FLUID, ++nfluid;
+      if (itf) f |= NF_ITF;
+      const bool inlet = fl && (tg & FSI_TAG_INLET);
+      if (inlet) f |= NF_U_INLET;
+      else if (itf) f |= NF_U_KIN;
+      if (wl && !fl) f |= NF_U_IDENT | NF_P_IDENT;
+      if (tg & (FSI_TAG_INLET | FSI_TAG_OUTLET | FSI_TAG_WALL_END)) f |= NF_D_ZERO;
+      if (wl && bc[p].rigid_wall) f |= NF_D_ZERO;
+      if (!fl && !wl) f |= NF_U_IDENT | NF_P_IDENT | NF_D_ZERO;  // isolated node
+      flag[i] = f;
+    }
+    std::vector<double> inl((size_t)INLET_STRIDE * n_problems);
+    for (int p = 0; p < n_problems; ++p) {
+      double* q = &inl[(size_t)INLET_STRIDE * p];
+      const double nn = std::sqrt(bc[p].normal[0] * bc[p].normal[0] + bc[p].normal[1] * bc[p].normal[1] +
+                                  bc[p].normal[2] * bc[p].normal[2]);
+      if (!(nn > 0) || !(bc[p].radius > 0)) throw StatusError{FSI_ERR_ARG, "inlet normal/radius invalid"};
+      for (int i = 0; i < 3; ++i) q[i] = bc[p].center[i], q[3 + i] = bc[p].normal[i] / nn;
+      q[6] = bc[p].radius;
+      q[7] = bc[p].peak;
+      q[8] = bc[p].amp;
+      q[9] = bc[p].freq;
+      q[10] = bc[p].phase;
+    }
+    cp->N = N;
+    cp->T = T0;
+    cp->Tf = Tf;
+    cp->n = 7 * N;
+    cp->nunk = 7 * nfluid + 3 * (N - nfluid);
+
+    // symbolic setup
+    BsrPattern P = build_pattern(N, tets);
+    std::vector<int64_t> bptr, nptr;
+    std::vector<int32_t> bsrc, nsrc;
+    build_gather(P, tets, bptr, bsrc, nptr, nsrc);
+    cp->nnzb = (int64_t)P.col.size();
+    cp->plan = build_ras(P, mesh->X, N, mesh->node_problem, n_problems, o.n_subdomains, o.overlap, o.ilu_level);
+
+    // device copies
+    std::vector<double> Xv(mesh->X, mesh->X + 3 * N);
+    cp->X = cp->upload(Xv);
+    cp->tets = cp->upload(tets);
+    cp->nflag = cp->upload(flag);
+    cp->nprobid = cp->upload(prob);
+    cp->inlet = cp->upload(inl);
+    cp->nptr = cp->upload(nptr);
+    cp->nsrc = cp->upload(nsrc);
+    cp->bptr = cp->upload(bptr);
+    cp->bsrc = cp->upload(bsrc);
+    cp->row_ptr = cp->upload(P.row_ptr);
+    cp->col = cp->upload(P.col);
+    cp->diag = cp->upload(P.diag);
+    const size_t vs = cp->mixed ? sizeof(float) : sizeof(double);
+    cp->Fe = cp->dalloc<double>(28 * T0);
+    cp->Ke = cp->dalloc<char>((int64_t)(784 * vs) * T0);
+    cp->vals = cp->dalloc<char>((int64_t)(49 * vs) * cp->nnzb);
+    CK(cudaMemsetAsync(cp->vals, 0, 49 * vs * cp->nnzb, cp->s));
+    cp->mesh = MeshDev{N, T0, Tf, cp->X, cp->tets, cp->nflag, cp->nprobid, cp->inlet};
+
+    const int64_t n = 7 * N;
+    cp->yn = cp->dalloc<double>(n);
+    cp->ynm1 = cp->dalloc<double>(n);
+    cp->ynm2 = cp->dalloc<double>(n);
+    CK(cudaMemsetAsync(cp->yn, 0, n * 8, cp->s));
+    CK(cudaMemsetAsync(cp->ynm1, 0, n * 8, cp->s));
+    CK(cudaMemsetAsync(cp->ynm2, 0, n * 8, cp->s));
+    cp->yk = cp->dalloc<double>(n);
+    cp->ytr = cp->dalloc<double>(n);
+    cp->F = cp->dalloc<double>(n);
+    cp->Ft = cp->dalloc<double>(n);
+    cp->dy = cp->dalloc<double>(n);
+    cp->rhs = cp->dalloc<double>(n);
+    const int32_t m = cp->m;
+    cp->V = cp->dalloc<double>((int64_t)(m + 1) * n);
+    cp->Z = cp->dalloc<double>((int64_t)m * n);
+    cp->H = cp->dalloc<double>((int64_t)(m + 1) * m);
+    cp->g = cp->dalloc<double>(m + 1);
+    cp->cs = cp->dalloc<double>(m);
+    cp->sn = cp->dalloc<double>(m);
+    cp->ylsq = cp->dalloc<double>(m);
+    cp->hA = cp->dalloc<double>(m + 1);
+    cp->hB = cp->dalloc<double>(m + 1);
+    cp->partial = cp->dalloc<double>((int64_t)RED_BLOCKS * (m + 2));
+    cp->scal = cp->dalloc<double>(4);
+    cp->r = cp->dalloc<double>(n);
+    CK(cudaMallocHost(&cp->hbuf, 64));
+
+    // Schwarz plan
+    RasPlan& R = cp->plan;
+    RasDev rd{};
+    rd.np = R.np;
+    rd.sd_row = cp->upload(R.sd_row);
+    rd.gnode = cp->upload(R.gnode);
+    rd.owned = cp->upload(R.owned);
+    rd.row_ptr = cp->upload(R.row_ptr);
+    rd.col = cp->upload(R.col);
+    rd.gblk = cp->upload(R.gblk);
+    rd.diag = cp->upload(R.diag);
+    rd.lent_ptr = cp->upload(R.lent_ptr);
+    rd.lent_pos = cp->upload(R.lent_pos);
+    rd.lent_kdiag = cp->upload(R.lent_kdiag);
+    rd.upd_ptr = cp->upload(R.upd_ptr);
+    rd.upd_tgt = cp->upload(R.upd_tgt);
+    rd.upd_src = cp->upload(R.upd_src);
+    rd.sd_lvlL = cp->upload(R.sd_lvlL);
+    rd.sd_lvlU = cp->upload(R.sd_lvlU);
+    rd.lvlL_ptr = cp->upload(R.lvlL_ptr);
+    rd.lvlU_ptr = cp->upload(R.lvlU_ptr);
+    rd.lvlL_rows = cp->upload(R.lvlL_rows);
+    rd.lvlU_rows = cp->upload(R.lvlU_rows);
+    rd.nblocks = (int64_t)R.col.size();
+    cp->ras = rd;
+    cp->fac = cp->dalloc<char>((int64_t)(49 * vs) * rd.nblocks);
+    cp->work = cp->dalloc<char>((int64_t)(7 * vs) * (int64_t)R.gnode.size());
+    cp->errflag = cp->dalloc<int32_t>(1);
+    CK(cudaStreamSynchronize(cp->s));
+    return FSI_OK;
+  });
+  if (st != FSI_OK) {
+    std::fprintf(stderr, "fsi_create: %s\n", cp->err.c_str());
+    fsi_destroy(c.release());
+    return st;
+  }
+  *out = c.release();
+  return FSI_OK;
+}
+
+fsi_status fsi_destroy(fsi_ctx* c) {
+  if (!c) return FSI_OK;
+  if (c->s) cudaStreamSynchronize(c->s);
+  else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->hbuf) cudaFreeHost(c->hbuf);
+  delete c;
+  return FSI_OK;
+}
+
+fsi_status fsi_set_state(fsi_ctx* c, const double* y_n, const double* y_nm1, const double* y_nm2, double t) {
+  if (!c || !y_n) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    CK(cudaMemcpyAsync(c->yn, y_n, c->n * 8, cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaMemcpyAsync(c->ynm1, y_nm1 ? y_nm1 : y_n, c->n * 8, cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaMemcpyAsync(c->ynm2, y_nm2 ? y_nm2 : (y_nm1 ? y_nm1 : y_n), c->n * 8, cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    c->t = t;
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_get_state(fsi_ctx* c, double* y_n, double* t) {
+  if (!c) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (y_n) CK(cudaMemcpyAsync(y_n, c->yn, c->n * 8, cudaMemcpyDeviceToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    if (t) *t = c->t;
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_residual(fsi_ctx* c, const double* y, double* F) {
+  if (!c || !y || !F) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    residual(c, y, F);
+    CK(cudaStreamSynchronize(c->s));
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_jacobian(fsi_ctx* c, const double* y) {
+  if (!c || !y) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    jacobian(c, y);
+    CK(cudaStreamSynchronize(c->s));
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_jacobian_export(fsi_ctx* c, int32_t* row_ptr, int32_t* col, double* vals) {
+  if (!c) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (row_ptr) {
+      std::vector<int64_t> rp(c->N + 1);
+      CK(cudaMemcpy(rp.data(), c->row_ptr, (c->N + 1) * 8, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i <= c->N; ++i) row_ptr[i] = (int32_t)rp[i];
+    }
+    if (col) CK(cudaMemcpy(col, c->col, c->nnzb * 4, cudaMemcpyDeviceToHost));
+    if (vals) {
+      CK(cudaStreamSynchronize(c->s));
+      if (c->mixed) {
+        std::vector<float> v(49 * c->nnzb);
+        CK(cudaMemcpy(v.data(), c->vals, v.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < v.size(); ++i) vals[i] = v[i];
+      } else {
+        CK(cudaMemcpy(vals, c->vals, 49 * c->nnzb * 8, cudaMemcpyDeviceToHost));
+      }
+    }
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_spmv(fsi_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
+    spmv(c, x, y);
+    CK(cudaStreamSynchronize(c->s));
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_pc_apply(fsi_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
+    if (c->pc_stale) pc_setup(c);
+    pc_apply(c, r, z);
+    CK(cudaStreamSynchronize(c->s));
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_linear_solve(fsi_ctx* c, const double* rhs, double* x, fsi_solve_stats* stats) {
+  if (!c || !rhs || !x) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    fsi_status s = gmres(c, rhs, x, stats);
+    CK(cudaStreamSynchronize(c->s));
+    if (s != FSI_OK) c->err = "GMRES reached its iteration limit";
+    return s;
+  });
+}
+
+fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
+  if (!c) return FSI_ERR_ARG;
+  fsi_step_stats S{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fsi_status st = guarded(c, [&]() -> fsi_status {
+    c->timing = stats != nullptr;
+    for (double& v : c->phase_ms) v = 0.0;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, c->s));
+    const int64_t n = c->n;
+    launch_copy(n, c->yn, c->yk, c->s);
+    residual(c, c->yk, c->F);
+    S.residual_evaluations++;
+    double nf = norm(c, c->F);
+    const double nf0 = nf;
+    S.fnorm0 = nf0;
+    if (!std::isfinite(nf)) throw StatusError{FSI_ERR_NONFINITE, "non-finite residual"};
+    const double stall = 1e-8;
+    int32_t it = 0;
+    bool conv = false;
+    while (true) {
+      if (nf <= c->opt.newton_rtol * nf0 || nf <= c->opt.newton_atol) {
+        conv = true;
+        break;
+      }
+      if (it >= c->opt.newton_maxit) break;
+      if (it % c->opt.jac_lag == 0) {
+        jacobian(c, c->yk);
+        S.jacobian_evaluations++;
+      }
+      launch_axpby(n, -1.0, c->F, 0.0, c->F, c->rhs, c->s);
+      fsi_solve_stats ls{};
+      fsi_status lst = gmres(c, c->rhs, c->dy, &ls);
+      if (lst != FSI_OK && lst != FSI_ERR_LINEAR_DIVERGED) return lst;
+      S.linear_iterations += ls.iterations;
+      if (c->opt.verbose)
+        std::fprintf(stderr, "  newton %d: |F| = %.6e, gmres %d its (%.2e -> %.2e)\n", it, nf, ls.iterations,
+                     ls.rnorm0, ls.rnorm);
+      // backtracking line search
+      double alpha = 1.0, nft = 0.0;
+      bool ok = false;
+      while (true) {
+        launch_axpby(n, 1.0, c->yk, alpha, c->dy, c->ytr, c->s);
+        residual(c, c->ytr, c->Ft);
+        S.residual_evaluations++;
+        nft = norm(c, c->Ft);
+        if (std::isfinite(nft) && nft <= (1.0 - 1e-4 * alpha) * nf) {
+          ok = true;
+          break;
+        }
+        alpha *= 0.5;
+        if (alpha < 1.0 / 1024.0) break;
+      }
+      if (!ok) {
+        if (nf <= stall * nf0) {
+          conv = true;  // |F| sits at the rounding floor of its assembly
+          break;
+        }
+        throw StatusError{FSI_ERR_LINESEARCH, "backtracking line search found no sufficient decrease"};
+      }
+      const bool stalled = nft > 0.5 * nf && nft <= stall * nf0;
+      std::swap(c->yk, c->ytr);
+      std::swap(c->F, c->Ft);
+      nf = nft;
+      ++it;
+      if (stalled) {
+        conv = true;
+        break;
+      }
+    }
+    S.newton_iterations = it;
+    S.fnorm = nf;
+    S.converged = conv ? 1 : 0;
+    if (!conv) throw StatusError{FSI_ERR_DIVERGED, "Newton reached its iteration limit"};
+    // shift time levels: y_{n-2} <- y_{n-1} <- y_n <- y
+    double* old2 = c->ynm2;
+    c->ynm2 = c->ynm1;
+    c->ynm1 = c->yn;
+    c->yn = c->yk;
+    c->yk = old2;
+    c->t += c->opt.dt;
+    CK(cudaEventRecord(e1, c->s));
+    c->resolve_phases();
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    S.t_total = ms;
+    return FSI_OK;
+  });
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->spans.clear();
+  c->evused = 0;
+  c->timing = false;
+  S.t_funceval = c->phase_ms[PH_FUNC];
+  S.t_jaceval = c->phase_ms[PH_JAC];
+  S.t_pcsetup = c->phase_ms[PH_PCSETUP];
+  S.t_pcapply = c->phase_ms[PH_PCAPPLY];
+  S.t_spmv = c->phase_ms[PH_SPMV];
+  S.t_orth = c->phase_ms[PH_ORTH];
+  if (stats) *stats = S;
+  return st;
+}
+
+fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
+  if (!c || !info) return FSI_ERR_ARG;
+  info->n_nodes = c->N;
+  info->n_tets = c->T;
+  info->n_unknowns = c->nunk;
+  info->nnzb = c->nnzb;
+  info->n_fluid_tets = c->Tf;
+  info->n_wall_tets = c->T - c->Tf;
+  info->n_problems = c->nprob;
+  info->n_subdomains = c->plan.np;
+  info->factor_blocks = (int64_t)c->plan.col.size();
+  info->max_levels = c->plan.max_levels;
+  info->device_bytes = c->dev_bytes;
+  return FSI_OK;
+}
+
+const char* fsi_last_error(const fsi_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Launch wrappers of the solver's CUDA kernels (definitions in assembly.cu,
+// sparse.cu, krylov.cu). All take raw device pointers and a stream.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "element.cuh"
+
+namespace fsi {
+
+// per-problem inflow data: center[3], normal[3], radius, peak, amp, freq, phase
+constexpr int INLET_STRIDE = 11;
+
+struct MeshDev {
+  int64_t N, T, Tf;          // nodes, tets, fluid tets (tets [0, Tf) fluid, [Tf, T) wall)
+  const double* X;           // [N*3]
+  const int32_t* tets;       // [T*4]
+  const uint32_t* nflag;     // [N]
+  const int32_t* nprob;      // [N]
+  const double* inlet;       // [nprob*INLET_STRIDE]
+};
+
+// ---- assembly (assembly.cu)
+void launch_elem_residual(const MeshDev& m, const MatConst& mc, const double* y, const double* y1,
+                          const double* y2, double* Fe, cudaStream_t s);
+void launch_gather_residual(const MeshDev& m, const int64_t* nptr, const int32_t* nsrc, const double* Fe,
+                            double* F, cudaStream_t s);
+void launch_constraint_residual(const MeshDev& m, const MatConst& mc, double t, const double* y,
+                                const double* y1, double* F, cudaStream_t s);
+template <class T>
+void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const double* y, const double* y1,
+                          const double* y2, T* Ke, cudaStream_t s);
+template <class T>
+void launch_gather_jacobian(int64_t nnzb, const int64_t* bptr, const int32_t* bsrc, const T* Ke, T* vals,
+                            cudaStream_t s);
+template <class T>
+void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int32_t* diag, T* vals,
+                                cudaStream_t s);
+
+// ---- sparse (sparse.cu)
+template <class T>
+void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const T* vals, const double* x,
+                     double* y, cudaStream_t s);
+
+struct RasDev {
+  int32_t np;
+  const int64_t* sd_row;
+  const int32_t* gnode;
+  const uint8_t* owned;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int64_t* gblk;
+  const int64_t* diag;
+  const int64_t* lent_ptr;
+  const int64_t* lent_pos;
+  const int64_t* lent_kdiag;
+  const int64_t* upd_ptr;
+  const int64_t* upd_tgt;
+  const int64_t* upd_src;
+  const int64_t* sd_lvlL;
+  const int64_t* sd_lvlU;
+  const int64_t* lvlL_ptr;
+  const int64_t* lvlU_ptr;
+  const int32_t* lvlL_rows;
+  const int32_t* lvlU_rows;
+  int64_t nblocks;
+};
+template <class TF, class TJ>
+void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s);
+template <class TF>
+void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
+template <class TF>
+void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s);
+
+// ---- Krylov / BLAS-1 (krylov.cu); vectors of n doubles
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs, fixed so that reductions are deterministic
+void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
+                 double* out, cudaStream_t s);
+void launch_maxpy(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h, double* w,
+                  cudaStream_t s);
+void launch_norm(int64_t n, const double* x, double* partial, double* out, cudaStream_t s);
+void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, cudaStream_t s);
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t s);
+void launch_copy(int64_t n, const double* x, double* y, cudaStream_t s);
+void launch_fill(int64_t n, double v, double* x, cudaStream_t s);
+void launch_axpy_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s);
+void launch_add_small(int32_t nv, const double* a, const double* b, double* out, cudaStream_t s);
+void launch_givens(double* H, int32_t ldh, int32_t j, double* cs, double* sn, double* g, double* res,
+                   cudaStream_t s);
+void launch_lsq(const double* H, int32_t ldh, int32_t k, const double* g, double* y, cudaStream_t s);
+
+}  // namespace fsi

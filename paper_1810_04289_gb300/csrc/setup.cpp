@@ -1,0 +1,331 @@
+// Host-side symbolic setup (see setup.h).
+#include "setup.h"
+
+#include <algorithm>
+#include <map>
+#include <cmath>
+#include <numeric>
+#include <stdexcept>
+
+namespace fsi {
+
+BsrPattern build_pattern(int64_t n, const std::vector<int32_t>& tets) {
+  const int64_t T = (int64_t)tets.size() / 4;
+  // count incident tets per node, gather neighbour candidates, sort-unique per row
+  std::vector<int64_t> deg(n + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a) deg[tets[4 * t + a] + 1] += 4;
+  for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  std::vector<int32_t> cand(deg[n]);
+  std::vector<int64_t> fill(deg.begin(), deg.end() - 1);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a) {
+      int32_t i = tets[4 * t + a];
+      for (int b = 0; b < 4; ++b) cand[fill[i]++] = tets[4 * t + b];
+    }
+  BsrPattern P;
+  P.n = n;
+  P.row_ptr.assign(n + 1, 0);
+  P.diag.assign(n, -1);
+  std::vector<int32_t> row;
+  P.col.reserve(deg[n] / 3);
+  for (int64_t i = 0; i < n; ++i) {
+    row.assign(cand.begin() + deg[i], cand.begin() + deg[i + 1]);
+    row.push_back((int32_t)i);
+    std::sort(row.begin(), row.end());
+    row.erase(std::unique(row.begin(), row.end()), row.end());
+    for (int32_t j : row) {
+      if (j == i) P.diag[i] = (int32_t)(P.col.size() - P.row_ptr[i]);
+      P.col.push_back(j);
+    }
+    P.row_ptr[i + 1] = (int64_t)P.col.size();
+  }
+  for (int64_t i = 0; i < n; ++i) P.diag[i] = (int32_t)(P.row_ptr[i] + P.diag[i]);
+  return P;
+}
+
+static inline int64_t find_block(const BsrPattern& P, int32_t i, int32_t j) {
+  const int32_t* b = P.col.data() + P.row_ptr[i];
+  const int32_t* e = P.col.data() + P.row_ptr[i + 1];
+  const int32_t* it = std::lower_bound(b, e, j);
+  if (it == e || *it != j) throw std::runtime_error("pattern lookup failed");
+  return (int64_t)(it - P.col.data());
+}
+
+void build_gather(const BsrPattern& P, const std::vector<int32_t>& tets, std::vector<int64_t>& bptr,
+                  std::vector<int32_t>& bsrc, std::vector<int64_t>& nptr, std::vector<int32_t>& nsrc) {
+  const int64_t T = (int64_t)tets.size() / 4;
+  const int64_t nnzb = (int64_t)P.col.size();
+  std::vector<int64_t> blk(16 * T);
+  bptr.assign(nnzb + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        int64_t k = find_block(P, tets[4 * t + a], tets[4 * t + b]);
+        blk[16 * t + 4 * a + b] = k;
+        bptr[k + 1]++;
+      }
+  for (int64_t k = 0; k < nnzb; ++k) bptr[k + 1] += bptr[k];
+  bsrc.assign(16 * T, 0);
+  std::vector<int64_t> f(bptr.begin(), bptr.end() - 1);
+  for (int64_t t = 0; t < T; ++t)
+    for (int s = 0; s < 16; ++s) bsrc[f[blk[16 * t + s]]++] = (int32_t)(16 * t + s);
+  nptr.assign(P.n + 1, 0);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a) nptr[tets[4 * t + a] + 1]++;
+  for (int64_t i = 0; i < P.n; ++i) nptr[i + 1] += nptr[i];
+  nsrc.assign(4 * T, 0);
+  std::vector<int64_t> g(nptr.begin(), nptr.end() - 1);
+  for (int64_t t = 0; t < T; ++t)
+    for (int a = 0; a < 4; ++a) nsrc[g[tets[4 * t + a]]++] = (int32_t)(4 * t + a);
+}
+
+// ---------------------------------------------------------------------------
+// Schwarz subdomains
+// ---------------------------------------------------------------------------
+
+// recursive coordinate bisection of `idx` into `parts` parts numbered from `first`
+static void rcb(const double* X, std::vector<int32_t>& idx, int64_t lo, int64_t hi, int32_t parts,
+                int32_t first, std::vector<int32_t>& owner) {
+  if (parts <= 1 || hi - lo <= 1) {
+    for (int64_t k = lo; k < hi; ++k) owner[idx[k]] = first;
+    return;
+  }
+  double bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
+  for (int64_t k = lo; k < hi; ++k)
+    for (int c = 0; c < 3; ++c) {
+      bmin[c] = std::min(bmin[c], X[3 * (int64_t)idx[k] + c]);
+      bmax[c] = std::max(bmax[c], X[3 * (int64_t)idx[k] + c]);
+    }
+  int ax = 0;
+  for (int c = 1; c < 3; ++c)
+    if (bmax[c] - bmin[c] > bmax[ax] - bmin[ax]) ax = c;
+  int32_t pl = parts / 2;
+  int64_t mid = lo + (int64_t)((double)(hi - lo) * pl / parts);
+  std::nth_element(idx.begin() + lo, idx.begin() + mid, idx.begin() + hi, [&](int32_t a, int32_t b) {
+    double xa = X[3 * (int64_t)a + ax], xb = X[3 * (int64_t)b + ax];
+    return xa < xb || (xa == xb && a < b);
+  });
+  rcb(X, idx, lo, mid, pl, first, owner);
+  rcb(X, idx, mid, hi, parts - pl, first + pl, owner);
+}
+
+RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t* node_problem,
+                  int32_t n_problems, int32_t np_req, int32_t overlap, int32_t fill_level) {
+  RasPlan R;
+  // 1. non-overlapping partition: subdomains shared out over the problems by
+  //    node count, then recursive coordinate bisection inside each problem
+  std::vector<std::vector<int32_t>> pnodes(n_problems);
+  for (int64_t i = 0; i < n; ++i) pnodes[node_problem ? node_problem[i] : 0].push_back((int32_t)i);
+  std::vector<int32_t> owner(n, -1);
+  int32_t next = 0;
+  for (int32_t p = 0; p < n_problems; ++p) {
+    if (pnodes[p].empty()) continue;
+    int32_t k = (int32_t)std::llround((double)np_req * (double)pnodes[p].size() / (double)n);
+    k = std::max<int32_t>(1, std::min<int32_t>(k, (int32_t)pnodes[p].size()));
+    rcb(X, pnodes[p], 0, (int64_t)pnodes[p].size(), k, next, owner);
+    next += k;
+  }
+  const int32_t np = next;
+  R.np = np;
+  std::vector<std::vector<int32_t>> own(np);
+  for (int64_t i = 0; i < n; ++i) own[owner[i]].push_back((int32_t)i);
+
+  std::vector<int32_t> loc(n, -1), mark(n, -1);
+  R.sd_row.assign(1, 0);
+  R.row_ptr.assign(1, 0);
+  R.lent_ptr.assign(1, 0);
+  R.upd_ptr.assign(1, 0);
+  R.sd_lvlL.assign(1, 0);
+  R.sd_lvlU.assign(1, 0);
+  R.lvlL_ptr.assign(1, 0);
+  R.lvlU_ptr.assign(1, 0);
+  for (int32_t s = 0; s < np; ++s) {
+    // 2. overlap: delta layers of graph neighbours (Sec. 3, Omega_i^delta)
+    std::vector<int32_t> nodes = own[s];
+    for (int32_t v : nodes) mark[v] = s;
+    size_t frontier = 0;
+    for (int32_t layer = 0; layer < overlap; ++layer) {
+      size_t end = nodes.size();
+      for (size_t q = frontier; q < end; ++q) {
+        int32_t v = nodes[q];
+        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+          int32_t w = P.col[e];
+          if (mark[w] != s) {
+            mark[w] = s;
+            nodes.push_back(w);
+          }
+        }
+      }
+      frontier = end;
+    }
+    const int64_t m = (int64_t)nodes.size();
+    // 3. reverse Cuthill-McKee order of the overlapped subgraph
+    for (int64_t q = 0; q < m; ++q) loc[nodes[q]] = (int32_t)q;
+    std::vector<int32_t> degl(m, 0);
+    for (int64_t q = 0; q < m; ++q) {
+      int32_t v = nodes[q];
+      for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e)
+        if (loc[P.col[e]] >= 0 && P.col[e] != v) degl[q]++;
+    }
+    std::vector<int32_t> order;
+    order.reserve(m);
+    std::vector<uint8_t> seen(m, 0);
+    std::vector<int32_t> nb;
+    while ((int64_t)order.size() < m) {
+      // start from an unvisited node of minimum degree (a pseudo-peripheral choice)
+      int32_t st = -1;
+      for (int64_t q = 0; q < m; ++q)
+        if (!seen[q] && (st < 0 || degl[q] < degl[st])) st = (int32_t)q;
+      // one BFS sweep to move the start to the far end of the component
+      {
+        std::vector<int32_t> bfs{st};
+        std::vector<uint8_t> s2(m, 0);
+        s2[st] = 1;
+        for (size_t h = 0; h < bfs.size(); ++h) {
+          int32_t v = nodes[bfs[h]];
+          for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+            int32_t w = loc[P.col[e]];
+            if (w >= 0 && !s2[w] && !seen[w]) {
+              s2[w] = 1;
+              bfs.push_back(w);
+            }
+          }
+        }
+        int32_t best = bfs.back();
+        // among the last BFS level pick the minimum degree node
+        st = best;
+      }
+      seen[st] = 1;
+      size_t head = order.size();
+      order.push_back(st);
+      while (head < order.size()) {
+        int32_t q = order[head++];
+        int32_t v = nodes[q];
+        nb.clear();
+        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+          int32_t w = loc[P.col[e]];
+          if (w >= 0 && !seen[w]) {
+            seen[w] = 1;
+            nb.push_back(w);
+          }
+        }
+        std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+          return degl[a] < degl[b] || (degl[a] == degl[b] && nodes[a] < nodes[b]);
+        });
+        order.insert(order.end(), nb.begin(), nb.end());
+      }
+    }
+    std::reverse(order.begin(), order.end());
+    std::vector<int32_t> perm(m);  // old local -> new local
+    for (int64_t q = 0; q < m; ++q) perm[order[q]] = (int32_t)q;
+    std::vector<int32_t> gn(m);
+    for (int64_t q = 0; q < m; ++q) gn[perm[q]] = nodes[q];
+    for (int64_t q = 0; q < m; ++q) loc[gn[q]] = (int32_t)q;
+
+    // 4. local pattern of J_i^delta = R_i^delta J (R_i^delta)^T with its
+    //    extraction map, extended by the symbolic level-of-fill ILU(k) pattern
+    //    (fill blocks start at zero: gblk = -1)
+    const int64_t r0 = R.sd_row.back();
+    std::vector<std::vector<int32_t>> rcol(m);
+    std::vector<std::vector<int32_t>> rlev(m);
+    std::vector<std::vector<int64_t>> rgb(m);
+    std::map<int32_t, std::pair<int32_t, int64_t>> row;
+    for (int64_t q = 0; q < m; ++q) {
+      int32_t v = gn[q];
+      R.gnode.push_back(v);
+      R.owned.push_back(owner[v] == s ? 1 : 0);
+      row.clear();
+      for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+        int32_t w = loc[P.col[e]];
+        if (w >= 0) row[w] = {0, e};
+      }
+      if (fill_level > 0) {
+        for (auto it = row.begin(); it != row.end() && it->first < q; ++it) {
+          const int32_t k = it->first;
+          const int32_t lqk = it->second.first;
+          for (size_t f = 0; f < rcol[k].size(); ++f) {
+            const int32_t j = rcol[k][f];
+            if (j <= k) continue;
+            const int32_t nl = lqk + rlev[k][f] + 1;
+            if (nl > fill_level) continue;
+            auto jt = row.find(j);
+            if (jt == row.end()) row[j] = {nl, -1};
+            else if (nl < jt->second.first) jt->second.first = nl;
+          }
+        }
+      }
+      rcol[q].reserve(row.size());
+      for (auto& kv : row) {
+        rcol[q].push_back(kv.first);
+        rlev[q].push_back(kv.second.first);
+        rgb[q].push_back(kv.second.second);
+      }
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      for (size_t f = 0; f < rcol[q].size(); ++f) {
+        if (rcol[q][f] == q) R.diag.push_back((int64_t)R.col.size());
+        R.col.push_back((int32_t)(r0 + rcol[q][f]));
+        R.gblk.push_back(rgb[q][f]);
+      }
+      R.row_ptr.push_back((int64_t)R.col.size());
+    }
+    // 5. ILU elimination lists and level schedules
+    std::vector<int32_t> levL(m, 0), levU(m, 0);
+    int32_t nlevL = 0, nlevU = 0;
+    for (int64_t q = 0; q < m; ++q) {
+      const int64_t rb = R.row_ptr[r0 + q], re = R.row_ptr[r0 + q + 1];
+      for (int64_t e = rb; e < re; ++e) {
+        const int64_t k = R.col[e] - r0;
+        if (k >= q) break;
+        levL[q] = std::max(levL[q], levL[k] + 1);
+        R.lent_pos.push_back(e);
+        R.lent_kdiag.push_back(R.diag[r0 + k]);
+        // updates A_qj -= A_qk A_kj for j > k in row k with (q, j) in the pattern
+        const int64_t kb = R.row_ptr[r0 + k], ke = R.row_ptr[r0 + k + 1];
+        int64_t pq = e + 1;
+        for (int64_t f = kb; f < ke; ++f) {
+          const int64_t j = R.col[f] - r0;
+          if (j <= k) continue;
+          while (pq < re && R.col[pq] - r0 < j) ++pq;
+          if (pq < re && R.col[pq] - r0 == j) {
+            R.upd_tgt.push_back(pq);
+            R.upd_src.push_back(f);
+          }
+        }
+        R.upd_ptr.push_back((int64_t)R.upd_tgt.size());
+      }
+      R.lent_ptr.push_back((int64_t)R.lent_pos.size());
+      nlevL = std::max(nlevL, levL[q] + 1);
+    }
+    for (int64_t q = m - 1; q >= 0; --q) {
+      const int64_t rb = R.row_ptr[r0 + q], re = R.row_ptr[r0 + q + 1];
+      for (int64_t e = rb; e < re; ++e) {
+        const int64_t j = R.col[e] - r0;
+        if (j > q) levU[q] = std::max(levU[q], levU[j] + 1);
+      }
+      nlevU = std::max(nlevU, levU[q] + 1);
+    }
+    auto emit_levels = [&](const std::vector<int32_t>& lev, int32_t nlev, std::vector<int64_t>& lptr,
+                           std::vector<int32_t>& lrows, std::vector<int64_t>& sdl) {
+      std::vector<int64_t> cnt(nlev + 1, 0);
+      for (int64_t q = 0; q < m; ++q) cnt[lev[q] + 1]++;
+      for (int32_t l = 0; l < nlev; ++l) cnt[l + 1] += cnt[l];
+      const int64_t base = (int64_t)lrows.size();
+      lrows.resize(base + m);
+      std::vector<int64_t> f(cnt.begin(), cnt.end() - 1);
+      for (int64_t q = 0; q < m; ++q) lrows[base + f[lev[q]]++] = (int32_t)q;
+      for (int32_t l = 0; l < nlev; ++l) lptr.push_back(base + cnt[l + 1]);
+      sdl.push_back((int64_t)lptr.size() - 1);
+    };
+    emit_levels(levL, nlevL, R.lvlL_ptr, R.lvlL_rows, R.sd_lvlL);
+    emit_levels(levU, nlevU, R.lvlU_ptr, R.lvlU_rows, R.sd_lvlU);
+    R.max_levels = std::max(R.max_levels, std::max(nlevL, nlevU));
+    R.max_rows = std::max<int64_t>(R.max_rows, m);
+    R.sd_row.push_back(r0 + m);
+    for (int64_t q = 0; q < m; ++q) loc[gn[q]] = -1;
+  }
+  return R;
+}
+
+}  // namespace fsi

@@ -1,0 +1,300 @@
+// Block-sparse (7x7 BSR) matrix-vector product and the restricted additive
+// Schwarz preconditioner of Sec. 3, Eq. 14-16, with block ILU(0) subdomain
+// solves: extraction of the overlapped submatrices J_i^delta, batched
+// level-scheduled factorisation (one CTA per subdomain), and the
+// level-scheduled forward/backward solves with the restricted (owned-rows-only)
+// prolongation.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace fsi {
+
+namespace {
+
+inline int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  const int64_t cap = 152 * 64;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// ---------------------------------------------------------------------------
+// SpMV: one warp per block row. Lane l < 28 owns output component r = l / 4 and
+// every fourth block (q = l % 4) of the row; its 7-term dot products run in the
+// value type T and accumulate in FP64; the four partial sums of a component are
+// combined by two shuffles. Lanes 28..31 idle.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col, const T* __restrict__ vals,
+                                                  const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int r = lane >> 2, q = lane & 3;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = warp0; row < n; row += nwarps) {
+    const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
+    double acc = 0.0;
+    if (lane < 28) {
+      for (int64_t b = b0 + q; b < b1; b += 4) {
+        const T* A = vals + 49 * b + 7 * r;
+        const double* xb = x + 7 * (int64_t)col[b];
+        T s = A[0] * T(xb[0]);
+#pragma unroll
+        for (int c = 1; c < 7; ++c) s += A[c] * T(xb[c]);
+        acc += (double)s;
+      }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (lane < 28 && q == 0) y[7 * row + r] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// RAS: extraction of J_i^delta = R_i^delta J (R_i^delta)^T (Eq. 15)
+// ---------------------------------------------------------------------------
+template <class TF, class TJ>
+__global__ void k_ras_extract(int64_t nblocks, const int64_t* __restrict__ gblk, const TJ* __restrict__ vals,
+                              TF* __restrict__ fac) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 49 * nblocks;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / 49;
+    const int e = (int)(idx - 49 * b);
+    const int64_t gb = gblk[b];
+    fac[idx] = gb >= 0 ? (TF)vals[49 * gb + e] : TF(0);
+  }
+}
+
+template <class TF> __device__ __forceinline__ TF tiny_pivot();
+template <> __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
+template <> __device__ __forceinline__ float tiny_pivot<float>() { return 1e-37f; }
+
+// In-place inverse of the 7x7 block B (row-major) by one warp: Gauss-Jordan with
+// partial pivoting on the augmented [B | I] in shared memory `aug` (7 x 14).
+template <class TF>
+__device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < 98; e += 32) {
+    const int r = e / 14, c = e - 14 * r;
+    aug[e] = c < 7 ? B[7 * r + c] : (c - 7 == r ? TF(1) : TF(0));
+  }
+  __syncwarp();
+  for (int k = 0; k < 7; ++k) {
+    // pivot search (lane 0), row swap
+    int piv = k;
+    if (lane == 0) {
+      TF best = fabs(aug[14 * k + k]);
+      for (int r = k + 1; r < 7; ++r) {
+        TF v = fabs(aug[14 * r + k]);
+        if (v > best) { best = v; piv = r; }
+      }
+      if (!(best > tiny_pivot<TF>())) atomicExch(err, 1);
+    }
+    piv = __shfl_sync(0xffffffffu, piv, 0);
+    if (piv != k && lane < 14) {
+      TF a = aug[14 * k + lane];
+      aug[14 * k + lane] = aug[14 * piv + lane];
+      aug[14 * piv + lane] = a;
+    }
+    __syncwarp();
+    const TF inv = TF(1) / aug[14 * k + k];
+    __syncwarp();
+    if (lane < 14) aug[14 * k + lane] *= inv;
+    __syncwarp();
+    // every lane reads the multipliers of its entries before any lane writes
+    TF fct[4];
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = lane + 32 * it;
+      fct[it] = e < 98 ? aug[14 * (e / 14) + k] : TF(0);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int e = lane + 32 * it;
+      if (e < 98) {
+        const int r = e / 14, c = e - 14 * r;
+        if (r != k) aug[e] -= fct[it] * aug[14 * k + c];
+      }
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < 49; e += 32) {
+    const int r = e / 7, c = e - 7 * r;
+    B[e] = aug[14 * r + 7 + c];
+  }
+  __syncwarp();
+}
+
+// Batched level-scheduled block ILU(0): grid = one CTA per subdomain; a warp
+// factors one row of the current level; levels are separated by __syncthreads.
+template <class TF>
+__global__ void __launch_bounds__(256) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err) {
+  __shared__ TF sA[8][49];
+  __shared__ TF sAug[8][98];
+  const int s = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = R.sd_row[s];
+  for (int64_t l = R.sd_lvlL[s]; l < R.sd_lvlL[s + 1]; ++l) {
+    const int64_t lb = R.lvlL_ptr[l], le = R.lvlL_ptr[l + 1];
+    for (int64_t ri = lb + warp; ri < le; ri += 8) {
+      const int64_t q = r0 + R.lvlL_rows[ri];
+      for (int64_t e = R.lent_ptr[q]; e < R.lent_ptr[q + 1]; ++e) {
+        TF* Aik = fac + 49 * R.lent_pos[e];
+        const TF* Dk = fac + 49 * R.lent_kdiag[e];
+        // A_ik <- A_ik D_k^{-1}
+        TF v0 = TF(0), v1 = TF(0);
+        {
+          const int e0 = lane, e1 = lane + 32;
+          const int r_0 = e0 / 7, c_0 = e0 - 7 * r_0;
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) v0 += Aik[7 * r_0 + mm] * Dk[7 * mm + c_0];
+          if (e1 < 49) {
+            const int r_1 = e1 / 7, c_1 = e1 - 7 * r_1;
+#pragma unroll
+            for (int mm = 0; mm < 7; ++mm) v1 += Aik[7 * r_1 + mm] * Dk[7 * mm + c_1];
+          }
+        }
+        __syncwarp();
+        sA[warp][lane] = v0;
+        Aik[lane] = v0;
+        if (lane + 32 < 49) {
+          sA[warp][lane + 32] = v1;
+          Aik[lane + 32] = v1;
+        }
+        __syncwarp();
+        // A_ij -= A_ik A_kj
+        for (int64_t u = R.upd_ptr[e]; u < R.upd_ptr[e + 1]; ++u) {
+          TF* Aij = fac + 49 * R.upd_tgt[u];
+          const TF* Akj = fac + 49 * R.upd_src[u];
+          for (int ee = lane; ee < 49; ee += 32) {
+            const int rr = ee / 7, cc = ee - 7 * rr;
+            TF acc = Aij[ee];
+#pragma unroll
+            for (int mm = 0; mm < 7; ++mm) acc -= sA[warp][7 * rr + mm] * Akj[7 * mm + cc];
+            Aij[ee] = acc;
+          }
+        }
+        __syncwarp();
+      }
+      warp_invert7<TF>(fac + 49 * R.diag[q], sAug[warp], err);
+    }
+    __syncthreads();
+  }
+}
+
+// Batched RAS apply: grid = one CTA per subdomain; 8-lane groups own one row
+// (lane c < 7 computes component c). work holds the subdomain vector.
+template <class TF>
+__global__ void __launch_bounds__(256) k_ras_apply(RasDev R, const TF* __restrict__ fac,
+                                                   const double* __restrict__ rin, TF* __restrict__ work,
+                                                   double* __restrict__ z) {
+  const int s = blockIdx.x;
+  const int64_t r0 = R.sd_row[s], m = R.sd_row[s + 1] - r0;
+  const int grp = threadIdx.x >> 3, c = threadIdx.x & 7;
+  const int ngrp = blockDim.x >> 3;
+  TF* w = work + 7 * r0;
+  // restriction R_i^delta r
+  for (int64_t idx = threadIdx.x; idx < 7 * m; idx += blockDim.x) {
+    const int64_t q = idx / 7;
+    const int cc = (int)(idx - 7 * q);
+    w[idx] = (TF)rin[7 * (int64_t)R.gnode[r0 + q] + cc];
+  }
+  __syncthreads();
+  // forward solve with the unit lower factor
+  for (int64_t l = R.sd_lvlL[s]; l < R.sd_lvlL[s + 1]; ++l) {
+    const int64_t lb = R.lvlL_ptr[l], le = R.lvlL_ptr[l + 1];
+    for (int64_t ri = lb + grp; ri < le; ri += ngrp) {
+      const int64_t q = R.lvlL_rows[ri];
+      const int64_t gq = r0 + q;
+      if (c < 7) {
+        TF acc = w[7 * q + c];
+        for (int64_t e = R.row_ptr[gq]; e < R.diag[gq]; ++e) {
+          const TF* A = fac + 49 * e + 7 * c;
+          const TF* xk = work + 7 * (int64_t)R.col[e];
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) acc -= A[mm] * xk[mm];
+        }
+        w[7 * q + c] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // backward solve with the upper factor and inverted pivots
+  for (int64_t l = R.sd_lvlU[s]; l < R.sd_lvlU[s + 1]; ++l) {
+    const int64_t lb = R.lvlU_ptr[l], le = R.lvlU_ptr[l + 1];
+    // rounds are uniform across the warp so that every lane joins the shuffles
+    for (int64_t base = lb; base < le; base += ngrp) {
+      const int64_t ri = base + grp;
+      const bool act = ri < le;
+      const int64_t q = act ? R.lvlU_rows[ri] : 0;
+      const int64_t gq = r0 + q;
+      TF acc = TF(0);
+      if (act && c < 7) {
+        acc = w[7 * q + c];
+        for (int64_t e = R.diag[gq] + 1; e < R.row_ptr[gq + 1]; ++e) {
+          const TF* A = fac + 49 * e + 7 * c;
+          const TF* xk = work + 7 * (int64_t)R.col[e];
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) acc -= A[mm] * xk[mm];
+        }
+      }
+      // z_q = D_q^{-1} t: gather t from the 7 lanes of the group
+      TF tv[7];
+#pragma unroll
+      for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, acc, (threadIdx.x & 31 & ~7) + mm);
+      if (act && c < 7) {
+        const TF* Dinv = fac + 49 * R.diag[gq] + 7 * c;
+        TF zz = TF(0);
+#pragma unroll
+        for (int mm = 0; mm < 7; ++mm) zz += Dinv[mm] * tv[mm];
+        w[7 * q + c] = zz;
+      }
+    }
+    __syncthreads();
+  }
+  // restricted prolongation (R_i^0)^T: owned rows only
+  for (int64_t idx = threadIdx.x; idx < 7 * m; idx += blockDim.x) {
+    const int64_t q = idx / 7;
+    const int cc = (int)(idx - 7 * q);
+    if (R.owned[r0 + q]) z[7 * (int64_t)R.gnode[r0 + q] + cc] = (double)w[idx];
+  }
+}
+
+}  // namespace
+
+template <class T>
+void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const T* vals, const double* x,
+                     double* y, cudaStream_t s) {
+  k_bsr_spmv<T><<<grid_for(32 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y);
+}
+
+template <class TF, class TJ>
+void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s) {
+  k_ras_extract<TF, TJ><<<grid_for(49 * r.nblocks, 256), 256, 0, s>>>(r.nblocks, r.gblk, vals, fac);
+}
+
+template <class TF>
+void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
+  k_ras_factor<TF><<<r.np, 256, 0, s>>>(r, fac, err);
+}
+
+template <class TF>
+void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s) {
+  k_ras_apply<TF><<<r.np, 256, 0, s>>>(r, fac, rin, work, z);
+}
+
+template void launch_bsr_spmv<double>(int64_t, const int64_t*, const int32_t*, const double*, const double*,
+                                      double*, cudaStream_t);
+template void launch_bsr_spmv<float>(int64_t, const int64_t*, const int32_t*, const float*, const double*,
+                                     double*, cudaStream_t);
+template void launch_ras_extract<double, double>(const RasDev&, const double*, double*, cudaStream_t);
+template void launch_ras_extract<float, float>(const RasDev&, const float*, float*, cudaStream_t);
+template void launch_ras_factor<double>(const RasDev&, double*, int32_t*, cudaStream_t);
+template void launch_ras_factor<float>(const RasDev&, float*, int32_t*, cudaStream_t);
+template void launch_ras_apply<double>(const RasDev&, const double*, const double*, double*, double*,
+                                       cudaStream_t);
+template void launch_ras_apply<float>(const RasDev&, const float*, const double*, float*, double*, cudaStream_t);
+
+}  // namespace fsi

@@ -1,0 +1,200 @@
+"""Parity of the CUDA solver (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances: FP64 assembly 1e-12 relative (max norm per field row group), FP64
+Newton solutions 1e-8 relative, mixed-precision Newton solutions 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import vesselmesh as vm
+from oracle import fsi_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_1810_04289_gb300 import fsi  # noqa: E402
+
+MAT = dict(O.DEFAULT_MATERIAL)
+GROUPS = {"u": [0, 1, 2], "p": [3], "d": [4, 5, 6]}
+
+
+def oracle_problem(m, dt=1e-3, rigid=False):
+    return O.Problem(m.X, m.tets, m.tet_domain, m.node_tag, m.node_problem, m.inlets, mat=MAT, dt=dt,
+                     rigid_wall=rigid)
+
+
+def perturbed_states(m, seed, scale=(3, 3, 3, 10, 1e-4, 1e-4, 1e-4)):
+    rng = np.random.default_rng(seed)
+    y0 = vm.poiseuille_state(m)
+    fl = ((m.node_tag & vm.FLUID) != 0)[:, None]
+    sc = np.array(scale)
+    out = []
+    for _ in range(3):
+        y = y0 + rng.normal(size=y0.shape) * sc
+        y[:, 0:4] *= fl                     # wall-only u, p slots stay 0
+        out.append(y)
+    return out
+
+
+def rel_by_group(a, b):
+    """max |a-b| / max |b| over each field group of the node-major (N,7) arrays."""
+    return {g: np.abs(a[:, c] - b[:, c]).max() / max(np.abs(b[:, c]).max(), 1e-300) for g, c in GROUPS.items()}
+
+
+def jac_rel_by_group(Jg, Jo):
+    D = (Jg - Jo).tocsr()
+    out = {}
+    for g, cols in GROUPS.items():
+        rows = np.concatenate([np.arange(c, Jo.shape[0], 7) for c in cols])
+        dm = abs(D[rows]).max() if D[rows].nnz else 0.0
+        om = abs(Jo[rows]).max()
+        out[g] = dm / om
+    return out
+
+
+@pytest.fixture(scope="module")
+def tube0():
+    return vm.tube_config("tube-12x8x4")
+
+
+def make_solver(m, **opt):
+    o = fsi.fsi_default_options(**opt)
+    return fsi.Solver(m, MAT, o)
+
+
+# ---------------------------------------------------------------------------
+# assembly
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1])
+def test_residual_matches_oracle(tube0, seed):
+    m = tube0
+    y, y1, y2 = perturbed_states(m, seed)
+    t1 = 0.25
+    P = oracle_problem(m)
+    Fo = P.residual(y, y1, y2, t1 + P.dt)
+    S = make_solver(m)
+    S.set_state(y1, y2, None, t=t1)
+    Fg = S.residual(y)
+    rel = rel_by_group(Fg, Fo)
+    assert all(v < 1e-12 for v in rel.values()), rel
+
+
+def test_residual_small_meshes_and_rigid_wall():
+    for m, rigid in ((vm.tube_mesh(2, 4, 1, 1, seed=5), False), (vm.tube_mesh(3, 6, 2, 2, seed=6), True)):
+        y, y1, y2 = perturbed_states(m, 3)
+        P = oracle_problem(m, rigid=rigid)
+        Fo = P.residual(y, y1, y2, 0.5 + P.dt)
+        S = fsi.Solver(m, MAT, fsi.fsi_default_options(n_subdomains=2), rigid_wall=rigid)
+        S.set_state(y1, y2, None, t=0.5)
+        rel = rel_by_group(S.residual(y), Fo)
+        assert all(v < 1e-12 for v in rel.values()), rel
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_jacobian_fp64_matches_oracle(tube0, seed):
+    m = tube0
+    y, y1, y2 = perturbed_states(m, 10 + seed)
+    P = oracle_problem(m)
+    Jo = P.jacobian(y, y1, y2, 0.25 + P.dt)
+    S = make_solver(m)
+    S.set_state(y1, y2, None, t=0.25)
+    S.jacobian(y)
+    Jg = S.jacobian_csr()
+    rel = jac_rel_by_group(Jg, Jo)
+    assert all(v < 1e-12 for v in rel.values()), rel
+
+
+def test_jacobian_mixed_is_fp32_accurate(tube0):
+    m = tube0
+    y, y1, y2 = perturbed_states(m, 20)
+    P = oracle_problem(m)
+    Jo = P.jacobian(y, y1, y2, 0.25 + P.dt)
+    S = make_solver(m, precision=1)
+    S.set_state(y1, y2, None, t=0.25)
+    S.jacobian(y)
+    rel = jac_rel_by_group(S.jacobian_csr(), Jo)
+    assert all(v < 2e-5 for v in rel.values()), rel
+
+
+def test_spmv_matches_oracle_product(tube0):
+    m = tube0
+    y, y1, y2 = perturbed_states(m, 30)
+    P = oracle_problem(m)
+    Jo = P.jacobian(y, y1, y2, 0.25 + P.dt)
+    S = make_solver(m)
+    S.set_state(y1, y2, None, t=0.25)
+    S.jacobian(y)
+    x = np.random.default_rng(31).normal(size=(m.n_nodes, 7))
+    out = S.vec()
+    fsi.fsi_spmv(S.ctx, S.vec(x), out)
+    ref = (Jo @ x.reshape(-1)).reshape(-1, 7)
+    rel = rel_by_group(out.cpu().numpy(), ref)
+    assert all(v < 1e-12 for v in rel.values()), rel
+
+
+# ---------------------------------------------------------------------------
+# linear solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,nsub", [(0, 1), (0, 4), (1, 4)])
+def test_linear_solve_matches_direct_solve(tube0, precision, nsub):
+    import scipy.sparse.linalg as spla
+    m = tube0
+    y, y1, y2 = perturbed_states(m, 40)
+    P = oracle_problem(m)
+    Jo = P.jacobian(y, y1, y2, 0.25 + P.dt)
+    b = P.residual(y, y1, y2, 0.25 + P.dt)
+    xo = spla.spsolve(Jo.tocsc(), b.reshape(-1)).reshape(-1, 7)
+    # an FP32 operator limits the attainable relative residual to ~1e-6
+    rtol = 1e-10 if precision == 0 else 1e-5
+    S = make_solver(m, precision=precision, n_subdomains=nsub, gmres_rtol=rtol, gmres_maxit=600)
+    S.set_state(y1, y2, None, t=0.25)
+    S.jacobian(y)
+    x = S.vec()
+    st = fsi.fsi_linear_solve(S.ctx, S.vec(b), x)
+    assert st.converged == 1 and st.rnorm <= rtol * st.rnorm0 * 1.0001
+    xg = x.cpu().numpy()
+    tol = 1e-6 if precision == 0 else 1e-2
+    rel = rel_by_group(xg, xo)
+    assert all(v < tol for v in rel.values()), (rel, st.iterations)
+
+
+# ---------------------------------------------------------------------------
+# Newton steps
+# ---------------------------------------------------------------------------
+def _oracle_steps(m, n):
+    P = oracle_problem(m)
+    y0 = vm.poiseuille_state(m)
+    return y0, [y for y, _ in O.run_steps(P, y0, n)]
+
+
+@pytest.fixture(scope="module")
+def oracle_tube0_steps(tube0):
+    return _oracle_steps(tube0, 5)
+
+
+def test_newton_steps_fp64_match_oracle(tube0, oracle_tube0_steps):
+    y0, ref = oracle_tube0_steps
+    S = make_solver(tube0, newton_rtol=1e-10, gmres_rtol=1e-6, n_subdomains=4)
+    S.set_state(y0, t=0.0)
+    for k in range(5):
+        st = S.step()
+        y, t = S.state()
+        rel = rel_by_group(y, ref[k])
+        assert st.converged == 1
+        assert all(v < 1e-8 for v in rel.values()), (k, rel)
+        assert abs(t - (k + 1) * 1e-3) < 1e-15
+
+
+def test_newton_steps_mixed_match_oracle(tube0, oracle_tube0_steps):
+    y0, ref = oracle_tube0_steps
+    S = make_solver(tube0, precision=1, newton_rtol=1e-10, gmres_rtol=1e-4, n_subdomains=4)
+    S.set_state(y0, t=0.0)
+    for k in range(5):
+        st = S.step()
+        y, _ = S.state()
+        rel = rel_by_group(y, ref[k])
+        assert st.converged == 1
+        assert all(v < 1e-6 for v in rel.values()), (k, rel)
