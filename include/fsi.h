@@ -137,8 +137,11 @@ typedef struct {
   int32_t residual_evaluations;
   int32_t converged;
   double fnorm0, fnorm;        /* ||F|| at the first and last Newton iterate */
-  /* device time per phase (ms), in the paper's timing categories (Table 7) */
+  /* device time per phase (ms), in the paper's timing categories (Table 7),
+   * and how many times each phase ran; t_total is the device time of the step */
   double t_funceval, t_jaceval, t_pcsetup, t_pcapply, t_spmv, t_orth, t_total;
+  int32_t n_funceval, n_jaceval, n_pcsetup, n_pcapply, n_spmv, n_orth;
+  int64_t kernel_launches;     /* CUDA kernels launched by the step */
 } fsi_step_stats;
 
 typedef struct {
@@ -146,6 +149,7 @@ typedef struct {
   int64_t n_fluid_tets, n_wall_tets;
   int32_t n_problems, n_subdomains;
   int64_t factor_blocks;       /* 7x7 blocks held by all subdomain factors */
+  int64_t factor_rows;         /* block rows of all overlapped subdomains */
   int32_t max_levels;          /* deepest level schedule over the subdomains */
   int64_t device_bytes;        /* device memory held by the context */
 } fsi_info;

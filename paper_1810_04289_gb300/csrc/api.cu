@@ -37,6 +37,8 @@ struct StatusError {
 
 }  // namespace
 
+enum { PH_FUNC = 0, PH_JAC, PH_PCSETUP, PH_PCAPPLY, PH_SPMV, PH_ORTH };
+
 struct fsi_ctx {
   cudaStream_t s = nullptr;
   fsi_options opt{};
@@ -92,6 +94,8 @@ struct fsi_ctx {
   };
   std::vector<Span> spans;
   double phase_ms[8] = {0};
+  int32_t phase_n[8] = {0};
+  int64_t launches = 0;
   bool timing = false;
 
   template <class U>
@@ -119,7 +123,8 @@ struct fsi_ctx {
     }
     return evpool[evused++];
   }
-  int begin_phase() {
+  int begin_phase(int phase) {
+    phase_n[phase]++;
     if (!timing) return -1;
     cudaEvent_t a = ev();
     CK(cudaEventRecord(a, s));
@@ -145,8 +150,6 @@ struct fsi_ctx {
     evused = 0;
   }
 };
-
-enum { PH_FUNC = 0, PH_JAC, PH_PCSETUP, PH_PCAPPLY, PH_SPMV, PH_ORTH };
 
 namespace {
 
@@ -180,7 +183,8 @@ void check_launch() { CK(cudaGetLastError()); }
 
 // ---- F(y) for the step ending at t_n + dt (previous levels y_n, y_{n-1})
 void residual(fsi_ctx* c, const double* y, double* F) {
-  int h = c->begin_phase();
+  c->launches += 3;
+  int h = c->begin_phase(PH_FUNC);
   launch_elem_residual(c->mesh, c->mc, y, c->yn, c->ynm1, c->Fe, c->s);
   launch_gather_residual(c->mesh, c->nptr, c->nsrc, c->Fe, F, c->s);
   launch_constraint_residual(c->mesh, c->mc, c->t + c->opt.dt, y, c->yn, F, c->s);
@@ -189,12 +193,14 @@ void residual(fsi_ctx* c, const double* y, double* F) {
 }
 
 double norm(fsi_ctx* c, const double* x) {
+  c->launches += 2;
   launch_norm(c->n, x, c->partial, c->scal, c->s);
   return read_scalar(c, c->scal);
 }
 
 void jacobian(fsi_ctx* c, const double* y) {
-  int h = c->begin_phase();
+  c->launches += 3;
+  int h = c->begin_phase(PH_JAC);
   if (c->mixed) {
     launch_elem_jacobian<float>(c->mesh, c->mc, y, c->yn, c->ynm1, (float*)c->Ke, c->s);
     launch_gather_jacobian<float>(c->nnzb, c->bptr, c->bsrc, (const float*)c->Ke, (float*)c->vals, c->s);
@@ -211,7 +217,8 @@ void jacobian(fsi_ctx* c, const double* y) {
 }
 
 void spmv(fsi_ctx* c, const double* x, double* y) {
-  int h = c->begin_phase();
+  c->launches += 1;
+  int h = c->begin_phase(PH_SPMV);
   if (c->mixed)
     launch_bsr_spmv<float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x, y, c->s);
   else
@@ -221,7 +228,8 @@ void spmv(fsi_ctx* c, const double* x, double* y) {
 }
 
 void pc_setup(fsi_ctx* c) {
-  int h = c->begin_phase();
+  c->launches += 2;
+  int h = c->begin_phase(PH_PCSETUP);
   CK(cudaMemsetAsync(c->errflag, 0, sizeof(int32_t), c->s));
   if (c->mixed) {
     launch_ras_extract<float, float>(c->ras, (const float*)c->vals, (float*)c->fac, c->s);
@@ -241,7 +249,8 @@ void pc_setup(fsi_ctx* c) {
 }
 
 void pc_apply(fsi_ctx* c, const double* rin, double* z) {
-  int h = c->begin_phase();
+  c->launches += 1;
+  int h = c->begin_phase(PH_PCAPPLY);
   if (c->mixed)
     launch_ras_apply<float>(c->ras, (const float*)c->fac, rin, (float*)c->work, z, c->s);
   else
@@ -258,6 +267,7 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
   if (c->pc_stale) pc_setup(c);
   const int64_t n = c->n;
   const int32_t m = c->m, ldh = m + 1;
+  c->launches += 1;
   launch_fill(n, 0.0, x, c->s);
   launch_copy(n, b, c->r, c->s);
   double beta = norm(c, c->r);
@@ -267,6 +277,7 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
   bool conv = beta <= target || beta == 0.0;
   while (!conv && it < c->opt.gmres_maxit) {
     // V_0 = r / beta ; g = beta e_1
+    c->launches += 2;
     launch_scale_inv(n, c->r, c->scal, c->V, c->s);
     launch_fill(ldh, 0.0, c->g, c->s);
     launch_copy(1, c->scal, c->g, c->s);
@@ -277,8 +288,9 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
       double* w = c->V + (int64_t)(j + 1) * n;
       pc_apply(c, vj, zj);
       spmv(c, zj, w);
-      int h = c->begin_phase();
+      int h = c->begin_phase(PH_ORTH);
       double* Hj = c->H + (int64_t)j * ldh;
+      c->launches += 11;
       launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hA, c->s);
       launch_maxpy(n, j + 1, c->V, n, c->hA, w, c->s);
       launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hB, c->s);
@@ -296,6 +308,7 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
       if (!(res > target)) break;
     }
     // x += Z y
+    c->launches += 2 + k;
     launch_lsq(c->H, ldh, k, c->g, c->ylsq, c->s);
     for (int32_t q = 0; q < k; ++q) {
       // y_q is on the device: x += y_q Z_q
@@ -303,6 +316,7 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
     }
     // true residual r = b - J x
     spmv(c, x, c->r);
+    c->launches += 1;
     launch_axpby(n, 1.0, b, -1.0, c->r, c->r, c->s);
     beta = norm(c, c->r);
     conv = beta <= target;
@@ -662,6 +676,8 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
   fsi_status st = guarded(c, [&]() -> fsi_status {
     c->timing = stats != nullptr;
     for (double& v : c->phase_ms) v = 0.0;
+    for (int32_t& v : c->phase_n) v = 0;
+    c->launches = 0;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, c->s));
@@ -686,6 +702,7 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
         jacobian(c, c->yk);
         S.jacobian_evaluations++;
       }
+      c->launches += 1;
       launch_axpby(n, -1.0, c->F, 0.0, c->F, c->rhs, c->s);
       fsi_solve_stats ls{};
       fsi_status lst = gmres(c, c->rhs, c->dy, &ls);
@@ -698,6 +715,7 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
       double alpha = 1.0, nft = 0.0;
       bool ok = false;
       while (true) {
+        c->launches += 1;
         launch_axpby(n, 1.0, c->yk, alpha, c->dy, c->ytr, c->s);
         residual(c, c->ytr, c->Ft);
         S.residual_evaluations++;
@@ -756,6 +774,13 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
   S.t_pcapply = c->phase_ms[PH_PCAPPLY];
   S.t_spmv = c->phase_ms[PH_SPMV];
   S.t_orth = c->phase_ms[PH_ORTH];
+  S.n_funceval = c->phase_n[PH_FUNC];
+  S.n_jaceval = c->phase_n[PH_JAC];
+  S.n_pcsetup = c->phase_n[PH_PCSETUP];
+  S.n_pcapply = c->phase_n[PH_PCAPPLY];
+  S.n_spmv = c->phase_n[PH_SPMV];
+  S.n_orth = c->phase_n[PH_ORTH];
+  S.kernel_launches = c->launches;
   if (stats) *stats = S;
   return st;
 }
@@ -771,6 +796,7 @@ fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
   info->n_problems = c->nprob;
   info->n_subdomains = c->plan.np;
   info->factor_blocks = (int64_t)c->plan.col.size();
+  info->factor_rows = (int64_t)c->plan.gnode.size();
   info->max_levels = c->plan.max_levels;
   info->device_bytes = c->dev_bytes;
   return FSI_OK;

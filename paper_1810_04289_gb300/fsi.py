@@ -60,14 +60,16 @@ class FsiStepStats(ctypes.Structure):
                 ("jacobian_evaluations", ctypes.c_int32), ("residual_evaluations", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double)] + \
                [(k, ctypes.c_double) for k in ("t_funceval", "t_jaceval", "t_pcsetup", "t_pcapply", "t_spmv",
-                                                "t_orth", "t_total")]
+                                                "t_orth", "t_total")] + \
+               [(k, ctypes.c_int32) for k in ("n_funceval", "n_jaceval", "n_pcsetup", "n_pcapply", "n_spmv",
+                                               "n_orth")] + [("kernel_launches", ctypes.c_int64)]
 
 
 class FsiInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("n_unknowns", ctypes.c_int64),
                 ("nnzb", ctypes.c_int64), ("n_fluid_tets", ctypes.c_int64), ("n_wall_tets", ctypes.c_int64),
                 ("n_problems", ctypes.c_int32), ("n_subdomains", ctypes.c_int32),
-                ("factor_blocks", ctypes.c_int64), ("max_levels", ctypes.c_int32),
+                ("factor_blocks", ctypes.c_int64), ("factor_rows", ctypes.c_int64), ("max_levels", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64)]
 
 
