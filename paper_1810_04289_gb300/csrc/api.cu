@@ -83,8 +83,10 @@ struct fsi_ctx {
   RasDev ras{};
   void* fac = nullptr;
   void* work = nullptr;
-  int32_t* errflag = nullptr;
+  int32_t* errflag = nullptr;  // [0] zero pivot in the factorisation, [1] bounded wait gave up in the apply
   bool pc_stale = true;
+  RasStreamDev rs{};
+  bool use_stream = false;
   // timing
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
@@ -238,6 +240,13 @@ void pc_setup(fsi_ctx* c) {
     launch_ras_extract<double, double>(c->ras, (const double*)c->vals, (double*)c->fac, c->s);
     launch_ras_factor<double>(c->ras, (double*)c->fac, c->errflag, c->s);
   }
+  if (c->use_stream) {
+    c->launches += 1;
+    if (c->mixed)
+      launch_pack_factors<float>(c->rs, (const float*)c->fac, c->s);
+    else
+      launch_pack_factors<double>(c->rs, (const double*)c->fac, c->s);
+  }
   check_launch();
   c->end_phase(h, PH_PCSETUP);
   int32_t e = 0;
@@ -251,10 +260,16 @@ void pc_setup(fsi_ctx* c) {
 void pc_apply(fsi_ctx* c, const double* rin, double* z) {
   c->launches += 1;
   int h = c->begin_phase(PH_PCAPPLY);
-  if (c->mixed)
+  if (c->use_stream) {
+    if (c->mixed)
+      CK(launch_ras_apply_stream<float>(c->rs, rin, z, c->errflag + 1, c->s));
+    else
+      CK(launch_ras_apply_stream<double>(c->rs, rin, z, c->errflag + 1, c->s));
+  } else if (c->mixed) {
     launch_ras_apply<float>(c->ras, (const float*)c->fac, rin, (float*)c->work, z, c->s);
-  else
+  } else {
     launch_ras_apply<double>(c->ras, (const double*)c->fac, rin, (double*)c->work, z, c->s);
+  }
   check_launch();
   c->end_phase(h, PH_PCAPPLY);
 }
@@ -320,6 +335,13 @@ fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
     launch_axpby(n, 1.0, b, -1.0, c->r, c->r, c->s);
     beta = norm(c, c->r);
     conv = beta <= target;
+  }
+  if (c->use_stream) {
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&c->hbuf[2], c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    std::memcpy(&e, &c->hbuf[2], sizeof(int32_t));
+    if (e) throw StatusError{FSI_ERR_TIMEOUT, "a bounded wait in the preconditioner apply gave up"};
   }
   if (st) {
     st->iterations = it;
@@ -551,7 +573,62 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->ras = rd;
     cp->fac = cp->dalloc<char>((int64_t)(49 * vs) * rd.nblocks);
     cp->work = cp->dalloc<char>((int64_t)(7 * vs) * (int64_t)R.gnode.size());
-    cp->errflag = cp->dalloc<int32_t>(1);
+    cp->errflag = cp->dalloc<int32_t>(2);
+    CK(cudaMemsetAsync(cp->errflag, 0, 2 * sizeof(int32_t), cp->s));
+
+    // packed factor streams for the TMA-fed apply
+    {
+      std::vector<int64_t> Lcnt(R.gnode.size()), Ucnt(R.gnode.size()), Loff(R.np), Uoff(R.np), Lsrc, Usrc;
+      std::vector<int32_t> Lcol, Ucol;
+      int64_t maxblk = 1;
+      for (int32_t sd = 0; sd < R.np; ++sd) {
+        const int64_t a = R.sd_row[sd], b = R.sd_row[sd + 1];
+        Loff[sd] = (int64_t)Lsrc.size();
+        for (int64_t q = a; q < b; ++q) {
+          for (int64_t e = R.row_ptr[q]; e < R.diag[q]; ++e) {
+            Lsrc.push_back(e);
+            Lcol.push_back((int32_t)(R.col[e] - a));
+          }
+          Lcnt[q] = R.diag[q] - R.row_ptr[q];
+          maxblk = std::max(maxblk, Lcnt[q]);
+        }
+        Uoff[sd] = (int64_t)Usrc.size();
+        for (int64_t q = b - 1; q >= a; --q) {
+          Usrc.push_back(R.diag[q]);
+          Ucol.push_back((int32_t)(q - a));
+          for (int64_t e = R.diag[q] + 1; e < R.row_ptr[q + 1]; ++e) {
+            Usrc.push_back(e);
+            Ucol.push_back((int32_t)(R.col[e] - a));
+          }
+          Ucnt[q] = R.row_ptr[q + 1] - R.diag[q];
+          maxblk = std::max(maxblk, Ucnt[q]);
+        }
+      }
+      RasStreamDev& rs = cp->rs;
+      rs.np = R.np;
+      rs.sd_row = rd.sd_row;
+      rs.gnode = rd.gnode;
+      rs.owned = rd.owned;
+      rs.L_cnt = cp->upload(Lcnt);
+      rs.U_cnt = cp->upload(Ucnt);
+      rs.L_off = cp->upload(Loff);
+      rs.U_off = cp->upload(Uoff);
+      rs.nL = (int64_t)Lsrc.size();
+      rs.nU = (int64_t)Usrc.size();
+      rs.Lsrc = cp->upload(Lsrc);
+      rs.Lcol = cp->upload(Lcol);
+      rs.Usrc = cp->upload(Usrc);
+      rs.Ucol = cp->upload(Ucol);
+      rs.stage_blocks = (int32_t)maxblk;
+      rs.max_rows = R.max_rows;
+      const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
+      cp->use_stream = sm <= 200 * 1024;
+      if (cp->use_stream) {
+        const int stride = cp->mixed ? 52 : 50;
+        rs.Lpack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nL, 1));
+        rs.Upack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nU, 1));
+      }
+    }
     CK(cudaStreamSynchronize(cp->s));
     return FSI_OK;
   });

@@ -72,6 +72,34 @@ void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s);
 
+// ---- streamed RAS apply (ras_stream.cu)
+struct RasStreamDev {
+  int32_t np;
+  const int64_t* sd_row;
+  const int32_t* gnode;
+  const uint8_t* owned;
+  const int64_t* L_cnt;   // [rows] L blocks of each row
+  const int64_t* U_cnt;   // [rows] 1 (inverted pivot) + U blocks of each row
+  const int64_t* L_off;   // [np] first packed L block of each subdomain
+  const int64_t* U_off;   // [np] first packed U block of each subdomain
+  void* Lpack;
+  void* Upack;
+  int64_t nL, nU;
+  const int64_t* Lsrc;    // [nL] factor block copied into each packed L block
+  const int32_t* Lcol;    // [nL] subdomain-relative column row
+  const int64_t* Usrc;
+  const int32_t* Ucol;
+  int32_t stage_blocks;   // blocks per ring stage (max blocks of a row)
+  int64_t max_rows;       // rows of the largest subdomain
+};
+template <class TF>
+size_t ras_stream_smem(const RasStreamDev& r);
+template <class TF>
+void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s);
+template <class TF>
+cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, int32_t* err,
+                                    cudaStream_t s);
+
 // ---- Krylov / BLAS-1 (krylov.cu); vectors of n doubles
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs, fixed so that reductions are deterministic
 void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
