@@ -570,6 +570,13 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     rd.lvlL_rows = cp->upload(R.lvlL_rows);
     rd.lvlU_rows = cp->upload(R.lvlU_rows);
     rd.nblocks = (int64_t)R.col.size();
+    {
+      int64_t mb = 1;
+      for (size_t q = 0; q + 1 < R.row_ptr.size(); ++q) mb = std::max(mb, R.row_ptr[q + 1] - R.row_ptr[q]);
+      rd.max_row_blocks = (int32_t)mb;
+      const int nw = cp->mixed ? ras_factor_warps<float>((int32_t)mb) : ras_factor_warps<double>((int32_t)mb);
+      if (nw < 1) throw StatusError{FSI_ERR_ARG, "ILU rows too long for the shared-memory factorisation"};
+    }
     cp->ras = rd;
     cp->fac = cp->dalloc<char>((int64_t)(49 * vs) * rd.nblocks);
     cp->work = cp->dalloc<char>((int64_t)(7 * vs) * (int64_t)R.gnode.size());
@@ -619,8 +626,54 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Lcol = cp->upload(Lcol);
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
-      rs.stage_blocks = (int32_t)maxblk;
+      const int64_t SB = std::max<int64_t>(maxblk, cp->mixed ? 128 : 64);
+      rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
+      // row groups per stage
+      std::vector<int64_t> gLp{0}, gLb, gLn, gUp{0}, gUb, gUn;
+      std::vector<int32_t> gLr, gUr;
+      for (int32_t sd = 0; sd < R.np; ++sd) {
+        const int64_t a = R.sd_row[sd], b = R.sd_row[sd + 1];
+        int64_t blk = Loff[sd], n = 0;
+        gLr.push_back(0);
+        gLb.push_back(blk);
+        for (int64_t q = a; q < b; ++q) {
+          if (n > 0 && n + Lcnt[q] > SB) {
+            gLn.push_back(n);
+            blk += n;
+            n = 0;
+            gLr.push_back((int32_t)(q - a));
+            gLb.push_back(blk);
+          }
+          n += Lcnt[q];
+        }
+        gLn.push_back(n);
+        gLp.push_back((int64_t)gLr.size());
+        blk = Uoff[sd];
+        n = 0;
+        gUr.push_back((int32_t)(b - 1 - a));
+        gUb.push_back(blk);
+        for (int64_t q = b - 1; q >= a; --q) {
+          if (n > 0 && n + Ucnt[q] > SB) {
+            gUn.push_back(n);
+            blk += n;
+            n = 0;
+            gUr.push_back((int32_t)(q - a));
+            gUb.push_back(blk);
+          }
+          n += Ucnt[q];
+        }
+        gUn.push_back(n);
+        gUp.push_back((int64_t)gUr.size());
+      }
+      rs.gL_ptr = cp->upload(gLp);
+      rs.gL_row = cp->upload(gLr);
+      rs.gL_blk = cp->upload(gLb);
+      rs.gL_nblk = cp->upload(gLn);
+      rs.gU_ptr = cp->upload(gUp);
+      rs.gU_row = cp->upload(gUr);
+      rs.gU_blk = cp->upload(gUb);
+      rs.gU_nblk = cp->upload(gUn);
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
       cp->use_stream = sm <= 200 * 1024;
       if (cp->use_stream) {

@@ -64,11 +64,14 @@ struct RasDev {
   const int32_t* lvlL_rows;
   const int32_t* lvlU_rows;
   int64_t nblocks;
+  int32_t max_row_blocks;  // most blocks in one factor row
 };
 template <class TF, class TJ>
 void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s);
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
+template <class TF>
+int ras_factor_warps(int32_t max_row_blocks);  // 0: rows too long for shared memory
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s);
 
@@ -89,8 +92,17 @@ struct RasStreamDev {
   const int32_t* Lcol;    // [nL] subdomain-relative column row
   const int64_t* Usrc;
   const int32_t* Ucol;
-  int32_t stage_blocks;   // blocks per ring stage (max blocks of a row)
+  int32_t stage_blocks;   // blocks per ring stage (>= the longest row)
   int64_t max_rows;       // rows of the largest subdomain
+  // row groups: consecutive rows whose blocks fit one stage, one bulk copy each
+  const int64_t* gL_ptr;  // [np+1] groups of each subdomain (L stream)
+  const int32_t* gL_row;  // [groups] first row (ascending; the group ends where the next starts)
+  const int64_t* gL_blk;  // [groups] first packed block
+  const int64_t* gL_nblk; // [groups] blocks in the group
+  const int64_t* gU_ptr;  // same for the U stream (rows descending)
+  const int32_t* gU_row;
+  const int64_t* gU_blk;
+  const int64_t* gU_nblk;
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);

@@ -80,6 +80,9 @@ __device__ __forceinline__ int blk_col(const TF* blk) {
 
 constexpr int NST = 4;  // ring stages
 
+// Each stage carries a group of consecutive rows of one stream (at most
+// stage_blocks blocks), so one bulk copy moves several rows and NST groups are
+// in flight ahead of the consumer.
 template <class TF>
 __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const double* __restrict__ rin,
                                                          double* __restrict__ z, int32_t* err) {
@@ -108,40 +111,31 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
   }
   __syncthreads();
 
-  // rows of the L stream with blocks, then all rows of the U stream, in stream order
   const int64_t* Lcnt = R.L_cnt + r0;
   const int64_t* Ucnt = R.U_cnt + r0;
-  const TF* Lbase = reinterpret_cast<const TF*>(R.Lpack) + (size_t)R.L_off[s] * STR;
-  const TF* Ubase = reinterpret_cast<const TF*>(R.Upack) + (size_t)R.U_off[s] * STR;
+  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack);
+  const TF* Upack = reinterpret_cast<const TF*>(R.Upack);
+  const int64_t gL0 = R.gL_ptr[s], gL1 = R.gL_ptr[s + 1];
+  const int64_t gU0 = R.gU_ptr[s], gU1 = R.gU_ptr[s + 1];
+  const int ngroups = (int)((gL1 - gL0) + (gU1 - gU0));
 
   if (warp == 1) {
     if (lane == 0) {
-      int it = 0;
       bool ok = true;
-      const TF* src = Lbase;
-      for (int q = 0; q < m && ok; ++q) {
-        const int nb = (int)Lcnt[q];
-        if (nb == 0) continue;
+      int it = 0;
+      for (; it < ngroups; ++it) {
+        const bool isL = it < gL1 - gL0;
+        const int64_t g = isL ? gL0 + it : gU0 + (it - (gL1 - gL0));
         const int st = it % NST;
         if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
         if (!ok) break;
+        const int64_t nb = isL ? R.gL_nblk[g] : R.gU_nblk[g];
         const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
         mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(ring + (size_t)st * R.stage_blocks * STR, src, bytes, &full[st]);
-        src += (size_t)nb * STR;
-        ++it;
-      }
-      src = Ubase;
-      for (int q = m - 1; q >= 0 && ok; --q) {
-        const int nb = (int)Ucnt[q];
-        const int st = it % NST;
-        if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
-        if (!ok) break;
-        const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
-        mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(ring + (size_t)st * R.stage_blocks * STR, src, bytes, &full[st]);
-        src += (size_t)nb * STR;
-        ++it;
+        if (bytes) {
+          const TF* src = (isL ? Lpack + (size_t)R.gL_blk[g] * STR : Upack + (size_t)R.gU_blk[g] * STR);
+          bulk_g2s(ring + (size_t)st * R.stage_blocks * STR, src, bytes, &full[st]);
+        }
       }
       if (!ok) atomicExch(err, 2);
       // drain: the last copy issued into each stage must land before the CTA
@@ -153,68 +147,97 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
 
   // consumer warp
   const int j = lane / 7, c = lane - 7 * (lane / 7);  // block slot 0..3 (4 = idle), component
-  int it = 0;
   bool ok = true;
+  int it = 0;
   // forward: w_q -= sum_k L_qk w_k
-  for (int q = 0; q < m; ++q) {
-    const int nb = (int)Lcnt[q];
-    if (nb == 0) continue;
+  for (int64_t g = gL0; g < gL1 && ok; ++g, ++it) {
     const int st = it % NST;
     ok = mbar_wait(&full[st], (it / NST) & 1);
     if (!ok) break;
     const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    TF acc = TF(0);
-    if (j < 4) {
-      for (int b = j; b < nb; b += 4) {
-        const TF* blk = stg + (size_t)b * STR;
-        const TF* xk = w + 7 * blk_col(blk);
-        const TF* a = blk + 7 * c;
+    const int qa = R.gL_row[g];
+    const int qend = (g + 1 < gL1) ? R.gL_row[g + 1] : m;   // exclusive, ascending
+    for (int q = qa; q < qend; ++q) {
+      const int nb = (int)Lcnt[q];
+      TF acc0 = TF(0), acc1 = TF(0);
+      if (j < 4) {
+        int b = j;
+        for (; b + 4 < nb; b += 8) {
+          const TF* b0 = stg + (size_t)b * STR;
+          const TF* b1 = b0 + 4 * STR;
+          const TF* x0 = w + 7 * blk_col(b0);
+          const TF* x1 = w + 7 * blk_col(b1);
 #pragma unroll
-        for (int mm = 0; mm < 7; ++mm) acc += a[mm] * xk[mm];
+          for (int mm = 0; mm < 7; ++mm) {
+            acc0 += b0[7 * c + mm] * x0[mm];
+            acc1 += b1[7 * c + mm] * x1[mm];
+          }
+        }
+        if (b < nb) {
+          const TF* b0 = stg + (size_t)b * STR;
+          const TF* x0 = w + 7 * blk_col(b0);
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) acc0 += b0[7 * c + mm] * x0[mm];
+        }
       }
+      TF acc = acc0 + acc1;
+      acc += __shfl_down_sync(0xffffffffu, acc, 14);
+      acc += __shfl_down_sync(0xffffffffu, acc, 7);
+      if (lane < 7 && nb > 0) w[7 * q + lane] -= acc;
+      __syncwarp();
+      stg += (size_t)nb * STR;
     }
-    acc += __shfl_down_sync(0xffffffffu, acc, 14);
-    acc += __shfl_down_sync(0xffffffffu, acc, 7);
-    __syncwarp();
-    if (lane < 7) w[7 * q + lane] -= acc;
-    __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    ++it;
   }
   // backward: w_q = D_q^{-1} (w_q - sum_j U_qj w_j)
-  for (int q = m - 1; q >= 0 && ok; --q) {
-    const int nb = (int)Ucnt[q];
+  for (int64_t g = gU0; g < gU1 && ok; ++g, ++it) {
     const int st = it % NST;
     ok = mbar_wait(&full[st], (it / NST) & 1);
     if (!ok) break;
     const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    TF acc = TF(0);
-    if (j < 4) {
-      for (int b = 1 + j; b < nb; b += 4) {
-        const TF* blk = stg + (size_t)b * STR;
-        const TF* xk = w + 7 * blk_col(blk);
-        const TF* a = blk + 7 * c;
+    const int qa = R.gU_row[g];                                // first (highest) row of the group
+    const int qend = (g + 1 < gU1) ? R.gU_row[g + 1] : -1;     // exclusive, descending
+    for (int q = qa; q > qend; --q) {
+      const int nb = (int)Ucnt[q];
+      TF acc0 = TF(0), acc1 = TF(0);
+      if (j < 4) {
+        int b = 1 + j;
+        for (; b + 4 < nb; b += 8) {
+          const TF* b0 = stg + (size_t)b * STR;
+          const TF* b1 = b0 + 4 * STR;
+          const TF* x0 = w + 7 * blk_col(b0);
+          const TF* x1 = w + 7 * blk_col(b1);
 #pragma unroll
-        for (int mm = 0; mm < 7; ++mm) acc += a[mm] * xk[mm];
+          for (int mm = 0; mm < 7; ++mm) {
+            acc0 += b0[7 * c + mm] * x0[mm];
+            acc1 += b1[7 * c + mm] * x1[mm];
+          }
+        }
+        if (b < nb) {
+          const TF* b0 = stg + (size_t)b * STR;
+          const TF* x0 = w + 7 * blk_col(b0);
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) acc0 += b0[7 * c + mm] * x0[mm];
+        }
       }
-    }
-    acc += __shfl_down_sync(0xffffffffu, acc, 14);
-    acc += __shfl_down_sync(0xffffffffu, acc, 7);
-    const TF t = (lane < 7) ? w[7 * q + lane] - acc : TF(0);
-    TF tv[7];
+      TF acc = acc0 + acc1;
+      acc += __shfl_down_sync(0xffffffffu, acc, 14);
+      acc += __shfl_down_sync(0xffffffffu, acc, 7);
+      const TF t = (lane < 7) ? w[7 * q + lane] - acc : TF(0);
+      TF tv[7];
 #pragma unroll
-    for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
-    __syncwarp();
-    if (lane < 7) {
-      const TF* D = stg + 7 * lane;  // block 0: inverted pivot
-      TF zz = TF(0);
+      for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
+      if (lane < 7) {
+        const TF* D = stg + 7 * lane;  // first block of the row: inverted pivot
+        TF zz = TF(0);
 #pragma unroll
-      for (int mm = 0; mm < 7; ++mm) zz += D[mm] * tv[mm];
-      w[7 * q + lane] = zz;
+        for (int mm = 0; mm < 7; ++mm) zz += D[mm] * tv[mm];
+        w[7 * q + lane] = zz;
+      }
+      __syncwarp();
+      stg += (size_t)nb * STR;
     }
-    __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    ++it;
   }
   if (!ok) {
     if (lane == 0) atomicExch(err, 2);

@@ -127,58 +127,75 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
   __syncwarp();
 }
 
-// Batched level-scheduled block ILU(0): grid = one CTA per subdomain; a warp
-// factors one row of the current level; levels are separated by __syncthreads.
+// Batched level-scheduled block ILU: grid = one CTA per subdomain (FW warps);
+// a warp factors one row of the current level with that row's blocks staged in
+// shared memory: for each L block (i,k) in column order it forms
+// A_ik <- A_ik D_k^{-1} and applies every update A_ij -= A_ik A_kj in one pass
+// (lane task = update x column), so each L block costs one round trip to the
+// finished rows k instead of one per update. Levels are separated by
+// __syncthreads.
+constexpr int FW = 4;
+
 template <class TF>
-__global__ void __launch_bounds__(256) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err) {
-  __shared__ TF sA[8][49];
-  __shared__ TF sAug[8][98];
-  const int s = blockIdx.x;
+__global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err,
+                                                        int32_t max_row_blocks) {
+  extern __shared__ __align__(16) unsigned char fsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  TF* sAug = reinterpret_cast<TF*>(fsm) + warp * 98;
+  TF* sRow = reinterpret_cast<TF*>(fsm) + nw * 98 + (size_t)warp * max_row_blocks * 49;
+  const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s];
   for (int64_t l = R.sd_lvlL[s]; l < R.sd_lvlL[s + 1]; ++l) {
     const int64_t lb = R.lvlL_ptr[l], le = R.lvlL_ptr[l + 1];
-    for (int64_t ri = lb + warp; ri < le; ri += 8) {
+    for (int64_t ri = lb + warp; ri < le; ri += nw) {
       const int64_t q = r0 + R.lvlL_rows[ri];
+      const int64_t rp = R.row_ptr[q];
+      const int nblk = (int)(R.row_ptr[q + 1] - rp);
+      for (int e = lane; e < 49 * nblk; e += 32) sRow[e] = fac[49 * rp + e];
+      __syncwarp();
       for (int64_t e = R.lent_ptr[q]; e < R.lent_ptr[q + 1]; ++e) {
-        TF* Aik = fac + 49 * R.lent_pos[e];
+        TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
         const TF* Dk = fac + 49 * R.lent_kdiag[e];
         // A_ik <- A_ik D_k^{-1}
         TF v0 = TF(0), v1 = TF(0);
         {
-          const int e0 = lane, e1 = lane + 32;
-          const int r_0 = e0 / 7, c_0 = e0 - 7 * r_0;
+          const int r_0 = lane / 7, c_0 = lane - 7 * r_0;
 #pragma unroll
           for (int mm = 0; mm < 7; ++mm) v0 += Aik[7 * r_0 + mm] * Dk[7 * mm + c_0];
-          if (e1 < 49) {
-            const int r_1 = e1 / 7, c_1 = e1 - 7 * r_1;
+          if (lane + 32 < 49) {
+            const int e1 = lane + 32, r_1 = e1 / 7, c_1 = e1 - 7 * r_1;
 #pragma unroll
             for (int mm = 0; mm < 7; ++mm) v1 += Aik[7 * r_1 + mm] * Dk[7 * mm + c_1];
           }
         }
         __syncwarp();
-        sA[warp][lane] = v0;
         Aik[lane] = v0;
-        if (lane + 32 < 49) {
-          sA[warp][lane + 32] = v1;
-          Aik[lane + 32] = v1;
-        }
+        if (lane + 32 < 49) Aik[lane + 32] = v1;
         __syncwarp();
-        // A_ij -= A_ik A_kj
-        for (int64_t u = R.upd_ptr[e]; u < R.upd_ptr[e + 1]; ++u) {
-          TF* Aij = fac + 49 * R.upd_tgt[u];
-          const TF* Akj = fac + 49 * R.upd_src[u];
-          for (int ee = lane; ee < 49; ee += 32) {
-            const int rr = ee / 7, cc = ee - 7 * rr;
-            TF acc = Aij[ee];
+        // A_ij -= A_ik A_kj for every update of this L block: task = (update, column)
+        const int64_t u0 = R.upd_ptr[e];
+        const int ntask = 7 * (int)(R.upd_ptr[e + 1] - u0);
+        for (int t = lane; t < ntask; t += 32) {
+          const int u = t / 7, cc = t - 7 * u;
+          TF* Aij = sRow + 49 * (R.upd_tgt[u0 + u] - rp) + cc;
+          const TF* Akj = fac + 49 * R.upd_src[u0 + u] + cc;
+          TF col[7];
 #pragma unroll
-            for (int mm = 0; mm < 7; ++mm) acc -= sA[warp][7 * rr + mm] * Akj[7 * mm + cc];
-            Aij[ee] = acc;
+          for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
+#pragma unroll
+          for (int rr = 0; rr < 7; ++rr) {
+            TF acc = Aij[7 * rr];
+#pragma unroll
+            for (int mm = 0; mm < 7; ++mm) acc -= Aik[7 * rr + mm] * col[mm];
+            Aij[7 * rr] = acc;
           }
         }
         __syncwarp();
       }
-      warp_invert7<TF>(fac + 49 * R.diag[q], sAug[warp], err);
+      warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
+      for (int e = lane; e < 49 * nblk; e += 32) fac[49 * rp + e] = sRow[e];
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -276,9 +293,28 @@ void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s
 }
 
 template <class TF>
-void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
-  k_ras_factor<TF><<<r.np, 256, 0, s>>>(r, fac, err);
+size_t ras_factor_smem_per_warp(int32_t max_row_blocks) {
+  return (size_t)98 * sizeof(TF) + (size_t)max_row_blocks * 49 * sizeof(TF);
 }
+
+// warps per factorisation CTA: up to FW, as many as the shared memory allows
+template <class TF>
+int ras_factor_warps(int32_t max_row_blocks) {
+  const size_t per = ras_factor_smem_per_warp<TF>(max_row_blocks);
+  int nw = (int)((size_t)(220 * 1024) / per);
+  return nw < 1 ? 0 : (nw > FW ? FW : nw);
+}
+
+template <class TF>
+void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
+  const int nw = ras_factor_warps<TF>(r.max_row_blocks);
+  const size_t sm = (size_t)nw * ras_factor_smem_per_warp<TF>(r.max_row_blocks);
+  cudaFuncSetAttribute(k_ras_factor<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ras_factor<TF><<<r.np, 32 * nw, sm, s>>>(r, fac, err, r.max_row_blocks);
+}
+
+template int ras_factor_warps<float>(int32_t);
+template int ras_factor_warps<double>(int32_t);
 
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s) {
