@@ -121,6 +121,9 @@ typedef struct {
   int32_t jac_lag;        /* reuse the Jacobian for this many Newton iterations (Eq. 12), >= 1 */
   int32_t ilu_level;      /* level of fill k of the subdomain block ILU(k), 0..3 (Sec. 4.3) */
   int32_t threads_per_row;/* BSR SpMV rows-to-threads mapping: 0 = auto */
+  int32_t ordering;       /* node order inside each subdomain (Sec. 4.5): 0 natural
+                             (global node order), 1 RCM, 2 RCM with lumen nodes
+                             before interface and wall nodes */
   int32_t verbose;        /* print per-iteration norms to stderr */
 } fsi_options;
 
@@ -138,8 +141,11 @@ typedef struct {
   int32_t converged;
   double fnorm0, fnorm;        /* ||F|| at the first and last Newton iterate */
   /* device time per phase (ms), in the paper's timing categories (Table 7),
-   * and how many times each phase ran; t_total is the device time of the step */
-  double t_funceval, t_jaceval, t_pcsetup, t_pcapply, t_spmv, t_orth, t_total;
+   * and how many times each phase ran; t_total is the device time of the step.
+   * The GMRES restart cycles run as captured CUDA graphs: their whole time
+   * (preconditioner applies, SpMVs, orthogonalisation) is t_krylov, and
+   * t_pcapply / t_spmv / t_orth only count work outside the graphs. */
+  double t_funceval, t_jaceval, t_pcsetup, t_pcapply, t_spmv, t_orth, t_total, t_krylov;
   int32_t n_funceval, n_jaceval, n_pcsetup, n_pcapply, n_spmv, n_orth;
   int64_t kernel_launches;     /* CUDA kernels launched by the step */
 } fsi_step_stats;
@@ -157,7 +163,7 @@ typedef struct {
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,
  * newton_maxit 20, gmres_restart 30, gmres_maxit 1000, n_subdomains 64,
  * overlap 1, precision 0, jac_lag 1, ilu_level 1 (the paper's default subdomain
- * solver, Sec. 4), threads_per_row 0. A negative ilu_level or overlap in the
+ * solver, Sec. 4), threads_per_row 0, ordering 0. A negative ilu_level or overlap in the
  * caller's options also selects the default. */
 void fsi_default_options(fsi_options *opts);
 

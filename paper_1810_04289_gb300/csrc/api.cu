@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -37,7 +38,7 @@ struct StatusError {
 
 }  // namespace
 
-enum { PH_FUNC = 0, PH_JAC, PH_PCSETUP, PH_PCAPPLY, PH_SPMV, PH_ORTH };
+enum { PH_FUNC = 0, PH_JAC, PH_PCSETUP, PH_PCAPPLY, PH_SPMV, PH_ORTH, PH_KRYLOV };
 
 struct fsi_ctx {
   cudaStream_t s = nullptr;
@@ -77,7 +78,15 @@ struct fsi_ctx {
   int32_t m = 30;
   double *V = nullptr, *Z = nullptr, *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *ylsq = nullptr;
   double *hA = nullptr, *hB = nullptr, *partial = nullptr, *scal = nullptr, *r = nullptr;
-  double* hbuf = nullptr;  // pinned host scalars
+  double* gtarget = nullptr;     // device copy of the GMRES stopping threshold
+  int* cyc = nullptr;            // [0] cycle active, [1] columns done in the cycle
+  float* zf = nullptr;           // FP32 copy of the SpMV input (mixed precision)
+  double* hbuf = nullptr;        // pinned host scalars
+  // one GMRES cycle captured as a CUDA graph
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_nodes = 0;
   // RAS
   RasPlan plan;
   RasDev ras{};
@@ -87,6 +96,7 @@ struct fsi_ctx {
   bool pc_stale = true;
   RasStreamDev rs{};
   bool use_stream = false;
+  bool use_graph = true;
   // timing
   std::vector<cudaEvent_t> evpool;
   size_t evused = 0;
@@ -196,7 +206,7 @@ void residual(fsi_ctx* c, const double* y, double* F) {
 
 double norm(fsi_ctx* c, const double* x) {
   c->launches += 2;
-  launch_norm(c->n, x, c->partial, c->scal, c->s);
+  launch_norm(c->n, x, c->partial, c->scal, nullptr, c->s);
   return read_scalar(c, c->scal);
 }
 
@@ -218,13 +228,25 @@ void jacobian(fsi_ctx* c, const double* y) {
   c->pc_stale = true;
 }
 
-void spmv(fsi_ctx* c, const double* x, double* y) {
+// y = J x on stream st. Mixed precision: x32 must hold the FP32 copy of x (if
+// x32 is null, it is made here from x).
+void spmv_on(fsi_ctx* c, const double* x, const float* x32, double* y, const int* guard, cudaStream_t st) {
+  if (c->mixed) {
+    if (!x32) {
+      c->launches += 1;
+      launch_to_float(c->n, x, c->zf, guard, st);
+      x32 = c->zf;
+    }
+    launch_bsr_spmv<float, float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x32, y, guard, st);
+  } else {
+    launch_bsr_spmv<double, double>(c->N, c->row_ptr, c->col, (const double*)c->vals, x, y, guard, st);
+  }
   c->launches += 1;
+}
+
+void spmv(fsi_ctx* c, const double* x, double* y) {
   int h = c->begin_phase(PH_SPMV);
-  if (c->mixed)
-    launch_bsr_spmv<float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x, y, c->s);
-  else
-    launch_bsr_spmv<double>(c->N, c->row_ptr, c->col, (const double*)c->vals, x, y, c->s);
+  spmv_on(c, x, nullptr, y, nullptr, c->s);
   check_launch();
   c->end_phase(h, PH_SPMV);
 }
@@ -257,84 +279,128 @@ void pc_setup(fsi_ctx* c) {
   c->pc_stale = false;
 }
 
-void pc_apply(fsi_ctx* c, const double* rin, double* z) {
+// z = B^{-1} r on stream st (z32: optional FP32 copy of z)
+void pc_apply_on(fsi_ctx* c, const double* rin, double* z, float* z32, const int* guard, cudaStream_t st) {
   c->launches += 1;
-  int h = c->begin_phase(PH_PCAPPLY);
   if (c->use_stream) {
     if (c->mixed)
-      CK(launch_ras_apply_stream<float>(c->rs, rin, z, c->errflag + 1, c->s));
+      CK(launch_ras_apply_stream<float>(c->rs, rin, z, z32, c->errflag + 1, guard, st));
     else
-      CK(launch_ras_apply_stream<double>(c->rs, rin, z, c->errflag + 1, c->s));
+      CK(launch_ras_apply_stream<double>(c->rs, rin, z, z32, c->errflag + 1, guard, st));
   } else if (c->mixed) {
-    launch_ras_apply<float>(c->ras, (const float*)c->fac, rin, (float*)c->work, z, c->s);
+    launch_ras_apply<float>(c->ras, (const float*)c->fac, rin, (float*)c->work, z, z32, guard, st);
   } else {
-    launch_ras_apply<double>(c->ras, (const double*)c->fac, rin, (double*)c->work, z, c->s);
+    launch_ras_apply<double>(c->ras, (const double*)c->fac, rin, (double*)c->work, z, z32, guard, st);
   }
+}
+
+void pc_apply(fsi_ctx* c, const double* rin, double* z) {
+  int h = c->begin_phase(PH_PCAPPLY);
+  pc_apply_on(c, rin, z, nullptr, nullptr, c->s);
   check_launch();
   c->end_phase(h, PH_PCAPPLY);
 }
 
+// One Arnoldi step j of the cycle (CGS2, normalisation, Givens), guarded.
+void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
+  const int64_t n = c->n;
+  const int32_t ldh = c->m + 1;
+  double* w = c->V + (int64_t)(j + 1) * n;
+  double* Hj = c->H + (int64_t)j * ldh;
+  launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hA, guard, st);
+  launch_maxpy(n, j + 1, c->V, n, c->hA, w, guard, st);
+  launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hB, guard, st);
+  launch_maxpy(n, j + 1, c->V, n, c->hB, w, guard, st);
+  launch_add_small(j + 1, c->hA, c->hB, Hj, guard, st);
+  launch_norm(n, w, c->partial, Hj + j + 1, guard, st);
+  launch_scale_inv(n, w, Hj + j + 1, w, guard, st);
+  launch_givens(c->H, ldh, j, c->cs, c->sn, c->g, c->scal + 1, c->gtarget, c->cyc, c->cyc + 1, st);
+  c->launches += 11;
+}
+
+// The kernels of one restart cycle, from V_0 = r / ||r|| to the true residual
+// of the updated iterate: c->rhs is b, c->dy is x, c->r the residual, c->scal[0]
+// its norm on entry and on exit.
+void cycle_kernels(fsi_ctx* c, cudaStream_t st) {
+  const int64_t n = c->n;
+  const int32_t m = c->m, ldh = m + 1;
+  const int* guard = c->cyc;
+  launch_scale_inv(n, c->r, c->scal, c->V, nullptr, st);
+  launch_cycle_init(c->g, ldh, c->scal, c->cyc, c->cyc + 1, st);
+  c->launches += 2;
+  for (int32_t j = 0; j < m; ++j) {
+    double* vj = c->V + (int64_t)j * n;
+    double* zj = c->Z + (int64_t)j * n;
+    double* w = c->V + (int64_t)(j + 1) * n;
+    pc_apply_on(c, vj, zj, c->mixed ? c->zf : nullptr, guard, st);
+    spmv_on(c, zj, c->mixed ? c->zf : nullptr, w, guard, st);
+    arnoldi_step(c, j, guard, st);
+  }
+  launch_lsq(c->H, ldh, 0, c->cyc + 1, c->g, c->ylsq, st);
+  launch_update_x(n, c->Z, n, c->ylsq, c->cyc + 1, c->dy, st);
+  c->launches += 2;
+  spmv_on(c, c->dy, nullptr, c->r, nullptr, st);
+  launch_axpby(n, 1.0, c->rhs, -1.0, c->r, c->r, st);
+  launch_norm(n, c->r, c->partial, c->scal, nullptr, st);
+  c->launches += 3;
+}
+
+void build_graph(fsi_ctx* c) {
+  if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  const int64_t before = c->launches;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  cycle_kernels(c, c->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  CK(e);
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->gexec, g, 0));
+  c->graph_nodes = c->launches - before;
+  c->launches = before;
+}
+
 // Right-preconditioned restarted flexible GMRES (FGMRES form: the preconditioned
 // directions Z are stored, so an FP32 preconditioner is allowed), classical
-// Gram-Schmidt applied twice, Givens rotations; stops on the true residual.
-fsi_status gmres(fsi_ctx* c, const double* b, double* x, fsi_solve_stats* st) {
+// Gram-Schmidt applied twice, Givens rotations; each restart cycle runs as one
+// captured CUDA graph; the host checks the true residual once per cycle.
+// Solves J x = b with b = c->rhs, x = c->dy.
+fsi_status gmres(fsi_ctx* c, fsi_solve_stats* st) {
   if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
   if (c->pc_stale) pc_setup(c);
   const int64_t n = c->n;
-  const int32_t m = c->m, ldh = m + 1;
   c->launches += 1;
-  launch_fill(n, 0.0, x, c->s);
-  launch_copy(n, b, c->r, c->s);
+  launch_fill(n, 0.0, c->dy, c->s);
+  launch_copy(n, c->rhs, c->r, c->s);
   double beta = norm(c, c->r);
   const double rnorm0 = beta;
   const double target = c->opt.gmres_rtol * beta;
+  CK(cudaMemcpyAsync(c->gtarget, &target, sizeof(double), cudaMemcpyHostToDevice, c->s));
   int32_t it = 0;
   bool conv = beta <= target || beta == 0.0;
+  if (c->use_graph && !c->gexec) build_graph(c);
   while (!conv && it < c->opt.gmres_maxit) {
-    // V_0 = r / beta ; g = beta e_1
-    c->launches += 2;
-    launch_scale_inv(n, c->r, c->scal, c->V, c->s);
-    launch_fill(ldh, 0.0, c->g, c->s);
-    launch_copy(1, c->scal, c->g, c->s);
-    int32_t k = 0;
-    for (int32_t j = 0; j < m && it < c->opt.gmres_maxit; ++j) {
-      double* vj = c->V + (int64_t)j * n;
-      double* zj = c->Z + (int64_t)j * n;
-      double* w = c->V + (int64_t)(j + 1) * n;
-      pc_apply(c, vj, zj);
-      spmv(c, zj, w);
-      int h = c->begin_phase(PH_ORTH);
-      double* Hj = c->H + (int64_t)j * ldh;
-      c->launches += 11;
-      launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hA, c->s);
-      launch_maxpy(n, j + 1, c->V, n, c->hA, w, c->s);
-      launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hB, c->s);
-      launch_maxpy(n, j + 1, c->V, n, c->hB, w, c->s);
-      launch_add_small(j + 1, c->hA, c->hB, Hj, c->s);
-      launch_norm(n, w, c->partial, Hj + j + 1, c->s);
-      launch_scale_inv(n, w, Hj + j + 1, w, c->s);
-      launch_givens(c->H, ldh, j, c->cs, c->sn, c->g, c->scal, c->s);
-      check_launch();
-      c->end_phase(h, PH_ORTH);
-      const double res = read_scalar(c, c->scal);
-      ++it;
-      k = j + 1;
-      if (c->opt.verbose) std::fprintf(stderr, "    gmres %d: %.3e (target %.3e)\n", it, res, target);
-      if (!(res > target)) break;
+    int h = c->begin_phase(PH_KRYLOV);
+    if (c->use_graph) {
+      CK(cudaGraphLaunch(c->gexec, c->s));
+      c->launches += c->graph_nodes;
+    } else {
+      cycle_kernels(c, c->s);
     }
-    // x += Z y
-    c->launches += 2 + k;
-    launch_lsq(c->H, ldh, k, c->g, c->ylsq, c->s);
-    for (int32_t q = 0; q < k; ++q) {
-      // y_q is on the device: x += y_q Z_q
-      launch_axpy_dev(n, c->ylsq + q, c->Z + (int64_t)q * n, x, c->s);
-    }
-    // true residual r = b - J x
-    spmv(c, x, c->r);
-    c->launches += 1;
-    launch_axpby(n, 1.0, b, -1.0, c->r, c->r, c->s);
-    beta = norm(c, c->r);
+    check_launch();
+    c->end_phase(h, PH_KRYLOV);
+    CK(cudaMemcpyAsync(&c->hbuf[3], c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(&c->hbuf[4], c->cyc + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    beta = c->hbuf[3];
+    int k = 0;
+    std::memcpy(&k, &c->hbuf[4], sizeof(int));
+    it += k;
+    c->phase_n[PH_PCAPPLY] += k;
+    c->phase_n[PH_SPMV] += k + 1;
+    c->phase_n[PH_ORTH] += k;
+    if (c->opt.verbose) std::fprintf(stderr, "    gmres cycle: %d its, |r| = %.3e (target %.3e)\n", k, beta, target);
     conv = beta <= target;
+    if (k == 0) break;  // no progress possible (breakdown at the first step)
   }
   if (c->use_stream) {
     int32_t e = 0;
@@ -366,6 +432,7 @@ void fill_defaults(fsi_options* o) {
   o->jac_lag = 1;
   o->ilu_level = 1;
   o->threads_per_row = 0;
+  o->ordering = 0;
   o->verbose = 0;
 }
 
@@ -405,6 +472,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (q.jac_lag > 0) o.jac_lag = q.jac_lag;
       if (q.ilu_level >= 0) o.ilu_level = q.ilu_level;
       o.threads_per_row = q.threads_per_row;
+      if (q.ordering >= 0 && q.ordering <= 2) o.ordering = q.ordering;
       o.verbose = q.verbose;
     }
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
@@ -495,7 +563,11 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     std::vector<int32_t> bsrc, nsrc;
     build_gather(P, tets, bptr, bsrc, nptr, nsrc);
     cp->nnzb = (int64_t)P.col.size();
-    cp->plan = build_ras(P, mesh->X, N, mesh->node_problem, n_problems, o.n_subdomains, o.overlap, o.ilu_level);
+    std::vector<uint8_t> rank(N);
+    for (int64_t i = 0; i < N; ++i)
+      rank[i] = (flag[i] & NF_ITF) ? 1 : ((flag[i] & NF_FLUID) ? 0 : 2);
+    cp->plan = build_ras(P, mesh->X, N, mesh->node_problem, n_problems, o.n_subdomains, o.overlap, o.ilu_level,
+                         o.ordering, rank.data());
 
     // device copies
     std::vector<double> Xv(mesh->X, mesh->X + 3 * N);
@@ -544,6 +616,9 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->partial = cp->dalloc<double>((int64_t)RED_BLOCKS * (m + 2));
     cp->scal = cp->dalloc<double>(4);
     cp->r = cp->dalloc<double>(n);
+    cp->gtarget = cp->dalloc<double>(1);
+    cp->cyc = cp->dalloc<int>(2);
+    cp->zf = cp->dalloc<float>(n);
     CK(cudaMallocHost(&cp->hbuf, 64));
 
     // Schwarz plan
@@ -574,8 +649,18 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       int64_t mb = 1;
       for (size_t q = 0; q + 1 < R.row_ptr.size(); ++q) mb = std::max(mb, R.row_ptr[q + 1] - R.row_ptr[q]);
       rd.max_row_blocks = (int32_t)mb;
-      const int nw = cp->mixed ? ras_factor_warps<float>((int32_t)mb) : ras_factor_warps<double>((int32_t)mb);
+      int64_t ml = 1, mu = 1, me = 1;
+      for (size_t q = 0; q + 1 < R.lent_ptr.size(); ++q) {
+        ml = std::max(ml, R.lent_ptr[q + 1] - R.lent_ptr[q]);
+        mu = std::max(mu, R.upd_ptr[R.lent_ptr[q + 1]] - R.upd_ptr[R.lent_ptr[q]]);
+      }
+      for (size_t e = 0; e + 1 < R.upd_ptr.size(); ++e) me = std::max(me, R.upd_ptr[e + 1] - R.upd_ptr[e]);
+      rd.max_row_lent = (int32_t)ml;
+      rd.max_row_upd = (int32_t)mu;
+      rd.max_entry_upd = (int32_t)me;
+      const int nw = cp->mixed ? ras_factor_warps<float>(rd, nullptr) : ras_factor_warps<double>(rd, nullptr);
       if (nw < 1) throw StatusError{FSI_ERR_ARG, "ILU rows too long for the shared-memory factorisation"};
+
     }
     cp->ras = rd;
     cp->fac = cp->dalloc<char>((int64_t)(49 * vs) * rd.nblocks);
@@ -626,7 +711,13 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Lcol = cp->upload(Lcol);
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
-      const int64_t SB = std::max<int64_t>(maxblk, cp->mixed ? 128 : 64);
+      // stage geometry: FSI_STAGE_BLOCKS / FSI_STAGES override the defaults (tuning)
+      int64_t sbdef = cp->mixed ? 128 : 64;
+      int nst = 4;
+      if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) sbdef = std::max(1, std::atoi(e));
+      if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));
+      const int64_t SB = std::max<int64_t>(maxblk, sbdef);
+      rs.nst = nst;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       // row groups per stage
@@ -674,9 +765,14 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.gU_row = cp->upload(gUr);
       rs.gU_blk = cp->upload(gUb);
       rs.gU_nblk = cp->upload(gUn);
+      int64_t mg = 1;
+      for (int32_t sd = 0; sd < R.np; ++sd)
+        mg = std::max(mg, (gLp[sd + 1] - gLp[sd]) + (gUp[sd + 1] - gUp[sd]));
+      rs.max_groups = (int32_t)mg;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
       cp->use_stream = sm <= 200 * 1024;
       if (cp->use_stream) {
+        CK(cp->mixed ? ras_stream_init<float>(rs) : ras_stream_init<double>(rs));
         const int stride = cp->mixed ? 52 : 50;
         rs.Lpack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nL, 1));
         rs.Upack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nU, 1));
@@ -698,6 +794,9 @@ fsi_status fsi_destroy(fsi_ctx* c) {
   if (!c) return FSI_OK;
   if (c->s) cudaStreamSynchronize(c->s);
   else cudaDeviceSynchronize();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->hbuf) cudaFreeHost(c->hbuf);
@@ -792,7 +891,9 @@ fsi_status fsi_pc_apply(fsi_ctx* c, const double* r, double* z) {
 fsi_status fsi_linear_solve(fsi_ctx* c, const double* rhs, double* x, fsi_solve_stats* stats) {
   if (!c || !rhs || !x) return FSI_ERR_ARG;
   return guarded(c, [&]() -> fsi_status {
-    fsi_status s = gmres(c, rhs, x, stats);
+    CK(cudaMemcpyAsync(c->rhs, rhs, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    fsi_status s = gmres(c, stats);
+    CK(cudaMemcpyAsync(x, c->dy, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
     CK(cudaStreamSynchronize(c->s));
     if (s != FSI_OK) c->err = "GMRES reached its iteration limit";
     return s;
@@ -835,7 +936,7 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
       c->launches += 1;
       launch_axpby(n, -1.0, c->F, 0.0, c->F, c->rhs, c->s);
       fsi_solve_stats ls{};
-      fsi_status lst = gmres(c, c->rhs, c->dy, &ls);
+      fsi_status lst = gmres(c, &ls);
       if (lst != FSI_OK && lst != FSI_ERR_LINEAR_DIVERGED) return lst;
       S.linear_iterations += ls.iterations;
       if (c->opt.verbose)
@@ -904,6 +1005,7 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
   S.t_pcapply = c->phase_ms[PH_PCAPPLY];
   S.t_spmv = c->phase_ms[PH_SPMV];
   S.t_orth = c->phase_ms[PH_ORTH];
+  S.t_krylov = c->phase_ms[PH_KRYLOV];
   S.n_funceval = c->phase_n[PH_FUNC];
   S.n_jaceval = c->phase_n[PH_JAC];
   S.n_pcsetup = c->phase_n[PH_PCSETUP];

@@ -38,9 +38,11 @@ void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int3
                                 cudaStream_t s);
 
 // ---- sparse (sparse.cu)
-template <class T>
-void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const T* vals, const double* x,
-                     double* y, cudaStream_t s);
+// y = J x; guard: optional device flag, the kernel does nothing while *guard == 0
+template <class TV, class TX>
+void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const TV* vals, const TX* x,
+                     double* y, const int* guard, cudaStream_t s);
+void launch_to_float(int64_t n, const double* x, float* y, const int* guard, cudaStream_t s);
 
 struct RasDev {
   int32_t np;
@@ -65,15 +67,19 @@ struct RasDev {
   const int32_t* lvlU_rows;
   int64_t nblocks;
   int32_t max_row_blocks;  // most blocks in one factor row
+  int32_t max_row_lent;    // most L blocks in one row
+  int32_t max_row_upd;     // most elimination updates in one row
+  int32_t max_entry_upd;   // most updates of one L block
 };
 template <class TF, class TJ>
 void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s);
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
 template <class TF>
-int ras_factor_warps(int32_t max_row_blocks);  // 0: rows too long for shared memory
+int ras_factor_warps(const RasDev& r, bool* all_out);  // 0: rows too long for shared memory
 template <class TF>
-void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s);
+void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,
+                      const int* guard, cudaStream_t s);
 
 // ---- streamed RAS apply (ras_stream.cu)
 struct RasStreamDev {
@@ -103,31 +109,43 @@ struct RasStreamDev {
   const int32_t* gU_row;
   const int64_t* gU_blk;
   const int64_t* gU_nblk;
+  int32_t max_groups;     // most L + U groups of one subdomain
+  int32_t nst;            // ring stages in flight (2..8)
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);
 template <class TF>
 void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s);
+// once per context: allow the apply kernel its dynamic shared memory
 template <class TF>
-cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, int32_t* err,
-                                    cudaStream_t s);
+cudaError_t ras_stream_init(const RasStreamDev& r);
+// z = B^{-1} r; z32 (optional) receives an FP32 copy; guard as for the SpMV
+template <class TF>
+cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, float* z32, int32_t* err,
+                                    const int* guard, cudaStream_t s);
 
-// ---- Krylov / BLAS-1 (krylov.cu); vectors of n doubles
+// ---- Krylov / BLAS-1 (krylov.cu); vectors of n doubles. guard: optional
+// device flag; guarded kernels do nothing while *guard == 0.
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs, fixed so that reductions are deterministic
 void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                 double* out, cudaStream_t s);
+                 double* out, const int* guard, cudaStream_t s);
 void launch_maxpy(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h, double* w,
-                  cudaStream_t s);
-void launch_norm(int64_t n, const double* x, double* partial, double* out, cudaStream_t s);
-void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, cudaStream_t s);
+                  const int* guard, cudaStream_t s);
+void launch_norm(int64_t n, const double* x, double* partial, double* out, const int* guard, cudaStream_t s);
+void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, const int* guard,
+                      cudaStream_t s);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out,
                   cudaStream_t s);
 void launch_copy(int64_t n, const double* x, double* y, cudaStream_t s);
 void launch_fill(int64_t n, double v, double* x, cudaStream_t s);
-void launch_axpy_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s);
-void launch_add_small(int32_t nv, const double* a, const double* b, double* out, cudaStream_t s);
+void launch_add_small(int32_t nv, const double* a, const double* b, double* out, const int* guard,
+                      cudaStream_t s);
+void launch_cycle_init(double* g, int32_t ldh, const double* scal, int* active, int* kcols, cudaStream_t s);
 void launch_givens(double* H, int32_t ldh, int32_t j, double* cs, double* sn, double* g, double* res,
-                   cudaStream_t s);
-void launch_lsq(const double* H, int32_t ldh, int32_t k, const double* g, double* y, cudaStream_t s);
+                   const double* target, int* active, int* kcols, cudaStream_t s);
+void launch_lsq(const double* H, int32_t ldh, int32_t k, const int* kdev, const double* g, double* y,
+                cudaStream_t s);
+void launch_update_x(int64_t n, const double* Z, int64_t ldz, const double* y, const int* kdev, double* x,
+                     cudaStream_t s);
 
 }  // namespace fsi

@@ -1,7 +1,12 @@
 // FP64 vector kernels of the Krylov loop: multi-dot products for classical
-// Gram-Schmidt (twice), multi-axpy, norms and scaling. Reductions use a fixed
-// grid of RED_BLOCKS blocks and a second pass in fixed order, so results are
-// bitwise reproducible run to run.
+// Gram-Schmidt (twice), multi-axpy, norms, scaling, Givens rotations and the
+// Hessenberg least-squares solve. Reductions use a fixed grid of RED_BLOCKS
+// blocks and a second pass in fixed order, so results are bitwise
+// reproducible run to run.
+//
+// Kernels that run inside a captured GMRES cycle take a guard pointer: while
+// *guard == 0 (the cycle has converged or broken down) they return at once, so
+// the remaining iterations of the captured cycle cost only their launches.
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -13,6 +18,8 @@ namespace {
 constexpr int RB = 256;   // threads per reduction block
 constexpr int MD = 8;     // vectors per multi-dot pass
 
+__device__ __forceinline__ bool off(const int* guard) { return guard && *guard == 0; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -22,7 +29,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial[blockIdx.x * ldp + k] = sum over this block's rows of V_k . w
 __global__ void __launch_bounds__(RB) k_mdot(int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
                                              const double* __restrict__ w, double* __restrict__ partial,
-                                             int32_t ldp) {
+                                             int32_t ldp, const int* guard) {
+  if (off(guard)) return;
   __shared__ double red[MD][RB / 32];
   const int k0 = blockIdx.y * MD;
   double acc[MD];
@@ -49,7 +57,8 @@ __global__ void __launch_bounds__(RB) k_mdot(int64_t n, int32_t nv, const double
 }
 
 __global__ void k_reduce_partials(int32_t nv, const double* __restrict__ partial, int32_t ldp, int32_t nb,
-                                  double* __restrict__ out, int take_sqrt) {
+                                  double* __restrict__ out, int take_sqrt, const int* guard) {
+  if (off(guard)) return;
   __shared__ double red[RB / 32];
   for (int k = 0; k < nv; ++k) {
     double v = 0.0;
@@ -68,7 +77,8 @@ __global__ void k_reduce_partials(int32_t nv, const double* __restrict__ partial
 
 // w -= sum_k h[k] V_k
 __global__ void k_maxpy(int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
-                        const double* __restrict__ h, double* __restrict__ w) {
+                        const double* __restrict__ h, double* __restrict__ w, const int* guard) {
+  if (off(guard)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = w[i];
     for (int k = 0; k < nv; ++k) s -= h[k] * V[(int64_t)k * ldv + i];
@@ -76,7 +86,9 @@ __global__ void k_maxpy(int64_t n, int32_t nv, const double* __restrict__ V, int
   }
 }
 
-__global__ void k_norm_partial(int64_t n, const double* __restrict__ x, double* __restrict__ partial) {
+__global__ void k_norm_partial(int64_t n, const double* __restrict__ x, double* __restrict__ partial,
+                               const int* guard) {
+  if (off(guard)) return;
   __shared__ double red[RB / 32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) acc += x[i] * x[i];
@@ -91,7 +103,8 @@ __global__ void k_norm_partial(int64_t n, const double* __restrict__ x, double* 
 }
 
 __global__ void k_scale_inv(int64_t n, const double* __restrict__ x, const double* __restrict__ scal,
-                            double* __restrict__ y) {
+                            double* __restrict__ y, const int* guard) {
+  if (off(guard)) return;
   const double a = *scal;
   const double inv = a != 0.0 ? 1.0 / a : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -109,26 +122,34 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ x) {
     x[i] = v;
 }
 
-__global__ void k_axpy_dev(int64_t n, const double* __restrict__ a, const double* __restrict__ x,
-                           double* __restrict__ y) {
-  const double av = *a;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += av * x[i];
-}
-
 // Hcol[k] = a[k] + b[k] (the two classical Gram-Schmidt passes)
 __global__ void k_add_small(int32_t nv, const double* __restrict__ a, const double* __restrict__ b,
-                            double* __restrict__ out) {
+                            double* __restrict__ out, const int* guard) {
+  if (off(guard)) return;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) out[k] = a[k] + b[k];
+}
+
+// start of a cycle: g = beta e_1 (beta = *scal), the cycle is active, no columns yet
+__global__ void k_cycle_init(double* __restrict__ g, int32_t ldh, const double* __restrict__ scal,
+                             int* __restrict__ active, int* __restrict__ kcols) {
+  for (int k = threadIdx.x; k < ldh; k += blockDim.x) g[k] = k == 0 ? *scal : 0.0;
+  if (threadIdx.x == 0) {
+    *active = 1;
+    *kcols = 0;
+  }
 }
 
 // Givens update of Hessenberg column j (column-major, leading dimension ldh):
 // apply the previous rotations, form the one that zeroes H[j+1][j], rotate the
-// right-hand side g, and return |g[j+1]| (the GMRES residual norm) in *res.
+// right-hand side g; |g[j+1]| is the GMRES residual norm. Stops the cycle when
+// it reaches *target or the Krylov space is exhausted (H[j+1][j] = 0).
 __global__ void k_givens(double* __restrict__ H, int32_t ldh, int32_t j, double* __restrict__ cs,
-                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res) {
+                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res,
+                         const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kcols) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (active && *active == 0) return;
   double* h = H + (int64_t)j * ldh;
+  const double sub = h[j + 1];
   for (int i = 0; i < j; ++i) {
     const double a = h[i], b = h[i + 1];
     h[i] = cs[i] * a + sn[i] * b;
@@ -148,18 +169,33 @@ __global__ void k_givens(double* __restrict__ H, int32_t ldh, int32_t j, double*
   const double gj = g[j];
   g[j] = c * gj;
   g[j + 1] = -sv * gj;
-  *res = fabs(g[j + 1]);
+  const double rn = fabs(g[j + 1]);
+  *res = rn;
+  if (kcols) *kcols = j + 1;
+  if (active && target && (!(rn > *target) || sub == 0.0)) *active = 0;
 }
 
-// y = R^{-1} g for the k x k upper-triangular rotated Hessenberg R
-__global__ void k_lsq(const double* __restrict__ H, int32_t ldh, int32_t k, const double* __restrict__ g,
-                      double* __restrict__ y) {
+// y = R^{-1} g for the k x k upper-triangular rotated Hessenberg R (k = *kdev if given)
+__global__ void k_lsq(const double* __restrict__ H, int32_t ldh, int32_t k, const int* __restrict__ kdev,
+                      const double* __restrict__ g, double* __restrict__ y) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (kdev) k = *kdev;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
     for (int jj = i + 1; jj < k; ++jj) s -= H[(int64_t)jj * ldh + i] * y[jj];
     const double d = H[(int64_t)i * ldh + i];
     y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+// x += sum_{q < k} y_q Z_q
+__global__ void k_update_x(int64_t n, const double* __restrict__ Z, int64_t ldz, const double* __restrict__ y,
+                           const int* __restrict__ kdev, double* __restrict__ x) {
+  const int k = *kdev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int q = 0; q < k; ++q) s += y[q] * Z[(int64_t)q * ldz + i];
+    x[i] = s;
   }
 }
 
@@ -172,24 +208,25 @@ inline int grid_for(int64_t work, int block) {
 }  // namespace
 
 void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                 double* out, cudaStream_t s) {
+                 double* out, const int* guard, cudaStream_t s) {
   dim3 grid(RED_BLOCKS, (nv + MD - 1) / MD);
-  k_mdot<<<grid, RB, 0, s>>>(n, nv, V, ldv, w, partial, nv);
-  k_reduce_partials<<<1, RB, 0, s>>>(nv, partial, nv, RED_BLOCKS, out, 0);
+  k_mdot<<<grid, RB, 0, s>>>(n, nv, V, ldv, w, partial, nv, guard);
+  k_reduce_partials<<<1, RB, 0, s>>>(nv, partial, nv, RED_BLOCKS, out, 0, guard);
 }
 
 void launch_maxpy(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h, double* w,
-                  cudaStream_t s) {
-  k_maxpy<<<grid_for(n, 256), 256, 0, s>>>(n, nv, V, ldv, h, w);
+                  const int* guard, cudaStream_t s) {
+  k_maxpy<<<grid_for(n, 256), 256, 0, s>>>(n, nv, V, ldv, h, w, guard);
 }
 
-void launch_norm(int64_t n, const double* x, double* partial, double* out, cudaStream_t s) {
-  k_norm_partial<<<RED_BLOCKS, RB, 0, s>>>(n, x, partial);
-  k_reduce_partials<<<1, RB, 0, s>>>(1, partial, 1, RED_BLOCKS, out, 1);
+void launch_norm(int64_t n, const double* x, double* partial, double* out, const int* guard, cudaStream_t s) {
+  k_norm_partial<<<RED_BLOCKS, RB, 0, s>>>(n, x, partial, guard);
+  k_reduce_partials<<<1, RB, 0, s>>>(1, partial, 1, RED_BLOCKS, out, 1, guard);
 }
 
-void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, cudaStream_t s) {
-  k_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(n, x, scal, y);
+void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, const int* guard,
+                      cudaStream_t s) {
+  k_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(n, x, scal, y, guard);
 }
 
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
@@ -204,21 +241,27 @@ void launch_fill(int64_t n, double v, double* x, cudaStream_t s) {
   k_fill<<<grid_for(n, 256), 256, 0, s>>>(n, v, x);
 }
 
-void launch_axpy_dev(int64_t n, const double* a, const double* x, double* y, cudaStream_t s) {
-  k_axpy_dev<<<grid_for(n, 256), 256, 0, s>>>(n, a, x, y);
+void launch_add_small(int32_t nv, const double* a, const double* b, double* out, const int* guard, cudaStream_t s) {
+  k_add_small<<<1, 64, 0, s>>>(nv, a, b, out, guard);
 }
 
-void launch_add_small(int32_t nv, const double* a, const double* b, double* out, cudaStream_t s) {
-  k_add_small<<<1, 64, 0, s>>>(nv, a, b, out);
+void launch_cycle_init(double* g, int32_t ldh, const double* scal, int* active, int* kcols, cudaStream_t s) {
+  k_cycle_init<<<1, 64, 0, s>>>(g, ldh, scal, active, kcols);
 }
 
 void launch_givens(double* H, int32_t ldh, int32_t j, double* cs, double* sn, double* g, double* res,
-                   cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, res);
+                   const double* target, int* active, int* kcols, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, res, target, active, kcols);
 }
 
-void launch_lsq(const double* H, int32_t ldh, int32_t k, const double* g, double* y, cudaStream_t s) {
-  k_lsq<<<1, 32, 0, s>>>(H, ldh, k, g, y);
+void launch_lsq(const double* H, int32_t ldh, int32_t k, const int* kdev, const double* g, double* y,
+                cudaStream_t s) {
+  k_lsq<<<1, 32, 0, s>>>(H, ldh, k, kdev, g, y);
+}
+
+void launch_update_x(int64_t n, const double* Z, int64_t ldz, const double* y, const int* kdev, double* x,
+                     cudaStream_t s) {
+  k_update_x<<<grid_for(n, 256), 256, 0, s>>>(n, Z, ldz, y, kdev, x);
 }
 
 }  // namespace fsi

@@ -78,24 +78,73 @@ __device__ __forceinline__ int blk_col(const TF* blk) {
   return *reinterpret_cast<const int*>(blk + 49);
 }
 
-constexpr int NST = 4;  // ring stages
+constexpr int NSTMAX = 8;  // most ring stages (runtime count R.nst)
+
+// sum over blocks b in [b0, nb) of (block b, row c) . w[col(b)], reduced over
+// the warp: lane = 7 j + c handles blocks b0 + j, b0 + j + 4, ...; every block
+// gathers its column index first so that all loads of a chunk are independent,
+// then forms the 7-term products as a short tree. The total lands in lanes 0..6.
+template <class TF, int STR>
+__device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w, int j, int c) {
+  TF acc = TF(0);
+  if (j < 4) {
+    for (int b = b0 + j; b < nb; b += 16) {
+      int cols[4];
+      const TF* blk[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int bi = b + 4 * i;
+        blk[i] = stg + (size_t)(bi < nb ? bi : b) * STR;
+        cols[i] = bi < nb ? blk_col(blk[i]) : -1;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (cols[i] >= 0) {
+          const TF* a = blk[i] + 7 * c;
+          const TF* x = w + 7 * cols[i];
+          const TF p01 = a[0] * x[0] + a[1] * x[1];
+          const TF p23 = a[2] * x[2] + a[3] * x[3];
+          const TF p45 = a[4] * x[4] + a[5] * x[5];
+          acc += (p01 + p23) + (p45 + a[6] * x[6]);
+        }
+      }
+    }
+  }
+  acc += __shfl_down_sync(0xffffffffu, acc, 14);
+  acc += __shfl_down_sync(0xffffffffu, acc, 7);
+  return acc;
+}
 
 // Each stage carries a group of consecutive rows of one stream (at most
 // stage_blocks blocks), so one bulk copy moves several rows and NST groups are
 // in flight ahead of the consumer.
 template <class TF>
 __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const double* __restrict__ rin,
-                                                         double* __restrict__ z, int32_t* err) {
+                                                         double* __restrict__ z, float* __restrict__ z32,
+                                                         int32_t* err, const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   constexpr int STR = Pack<TF>::stride;
   extern __shared__ __align__(128) unsigned char smem[];
+  const int NST = R.nst;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + NST;
+  uint64_t* empty = full + NSTMAX;
   TF* ring = reinterpret_cast<TF*>(smem + 128);
   TF* w = ring + (size_t)NST * R.stage_blocks * STR;
   const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s];
   const int m = (int)(R.sd_row[s + 1] - r0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-row block counts of both streams and the group table, next to the vector
+  unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 7 * (size_t)R.max_rows);
+  unsigned short* Ucnt = Lcnt + R.max_rows;
+  int* grow = reinterpret_cast<int*>(Ucnt + R.max_rows);  // 4-byte aligned: 2 x max_rows shorts
+  int* gblk = grow + R.max_groups;
+  int* gnb = gblk + R.max_groups;
+  const int64_t gL0 = R.gL_ptr[s], gL1 = R.gL_ptr[s + 1];
+  const int64_t gU0 = R.gU_ptr[s], gU1 = R.gU_ptr[s + 1];
+  const int nGL = (int)(gL1 - gL0);
+  const int ngroups = nGL + (int)(gU1 - gU0);
+  const int64_t Lb0 = R.L_off[s], Ub0 = R.U_off[s];
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NST; ++i) {
@@ -105,35 +154,40 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // restriction R_i^delta r into shared memory
-  for (int idx = threadIdx.x; idx < 7 * m; idx += blockDim.x) {
-    const int q = idx / 7, c = idx - 7 * q;
-    w[idx] = (TF)rin[7 * (int64_t)R.gnode[r0 + q] + c];
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    const double* src = rin + 7 * (int64_t)R.gnode[r0 + q];
+    double v[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) v[c] = src[c];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) w[7 * q + c] = (TF)v[c];
+    Lcnt[q] = (unsigned short)R.L_cnt[r0 + q];
+    Ucnt[q] = (unsigned short)R.U_cnt[r0 + q];
+  }
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const bool isL = g < nGL;
+    const int64_t gg = isL ? gL0 + g : gU0 + (g - nGL);
+    grow[g] = isL ? R.gL_row[gg] : R.gU_row[gg];
+    gblk[g] = (int)(isL ? R.gL_blk[gg] - Lb0 : R.gU_blk[gg] - Ub0);
+    gnb[g] = (int)(isL ? R.gL_nblk[gg] : R.gU_nblk[gg]);
   }
   __syncthreads();
 
-  const int64_t* Lcnt = R.L_cnt + r0;
-  const int64_t* Ucnt = R.U_cnt + r0;
-  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack);
-  const TF* Upack = reinterpret_cast<const TF*>(R.Upack);
-  const int64_t gL0 = R.gL_ptr[s], gL1 = R.gL_ptr[s + 1];
-  const int64_t gU0 = R.gU_ptr[s], gU1 = R.gU_ptr[s + 1];
-  const int ngroups = (int)((gL1 - gL0) + (gU1 - gU0));
+  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack) + (size_t)Lb0 * STR;
+  const TF* Upack = reinterpret_cast<const TF*>(R.Upack) + (size_t)Ub0 * STR;
 
   if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
       int it = 0;
       for (; it < ngroups; ++it) {
-        const bool isL = it < gL1 - gL0;
-        const int64_t g = isL ? gL0 + it : gU0 + (it - (gL1 - gL0));
         const int st = it % NST;
         if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
         if (!ok) break;
-        const int64_t nb = isL ? R.gL_nblk[g] : R.gU_nblk[g];
-        const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
+        const uint32_t bytes = (uint32_t)(gnb[it] * STR * sizeof(TF));
         mbar_arrive_expect_tx(&full[st], bytes);
         if (bytes) {
-          const TF* src = (isL ? Lpack + (size_t)R.gL_blk[g] * STR : Upack + (size_t)R.gU_blk[g] * STR);
+          const TF* src = (it < nGL ? Lpack : Upack) + (size_t)gblk[it] * STR;
           bulk_g2s(ring + (size_t)st * R.stage_blocks * STR, src, bytes, &full[st]);
         }
       }
@@ -150,39 +204,16 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
   bool ok = true;
   int it = 0;
   // forward: w_q -= sum_k L_qk w_k
-  for (int64_t g = gL0; g < gL1 && ok; ++g, ++it) {
+  for (; it < nGL && ok; ++it) {
     const int st = it % NST;
     ok = mbar_wait(&full[st], (it / NST) & 1);
     if (!ok) break;
     const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    const int qa = R.gL_row[g];
-    const int qend = (g + 1 < gL1) ? R.gL_row[g + 1] : m;   // exclusive, ascending
+    const int qa = grow[it];
+    const int qend = (it + 1 < nGL) ? grow[it + 1] : m;   // exclusive, ascending
     for (int q = qa; q < qend; ++q) {
-      const int nb = (int)Lcnt[q];
-      TF acc0 = TF(0), acc1 = TF(0);
-      if (j < 4) {
-        int b = j;
-        for (; b + 4 < nb; b += 8) {
-          const TF* b0 = stg + (size_t)b * STR;
-          const TF* b1 = b0 + 4 * STR;
-          const TF* x0 = w + 7 * blk_col(b0);
-          const TF* x1 = w + 7 * blk_col(b1);
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) {
-            acc0 += b0[7 * c + mm] * x0[mm];
-            acc1 += b1[7 * c + mm] * x1[mm];
-          }
-        }
-        if (b < nb) {
-          const TF* b0 = stg + (size_t)b * STR;
-          const TF* x0 = w + 7 * blk_col(b0);
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) acc0 += b0[7 * c + mm] * x0[mm];
-        }
-      }
-      TF acc = acc0 + acc1;
-      acc += __shfl_down_sync(0xffffffffu, acc, 14);
-      acc += __shfl_down_sync(0xffffffffu, acc, 7);
+      const int nb = Lcnt[q];
+      const TF acc = row_dot<TF, STR>(stg, 0, nb, w, j, c);
       if (lane < 7 && nb > 0) w[7 * q + lane] -= acc;
       __syncwarp();
       stg += (size_t)nb * STR;
@@ -190,39 +221,16 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     if (lane == 0) mbar_arrive(&empty[st]);
   }
   // backward: w_q = D_q^{-1} (w_q - sum_j U_qj w_j)
-  for (int64_t g = gU0; g < gU1 && ok; ++g, ++it) {
+  for (; it < ngroups && ok; ++it) {
     const int st = it % NST;
     ok = mbar_wait(&full[st], (it / NST) & 1);
     if (!ok) break;
     const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    const int qa = R.gU_row[g];                                // first (highest) row of the group
-    const int qend = (g + 1 < gU1) ? R.gU_row[g + 1] : -1;     // exclusive, descending
+    const int qa = grow[it];                                  // first (highest) row of the group
+    const int qend = (it + 1 < ngroups) ? grow[it + 1] : -1;  // exclusive, descending
     for (int q = qa; q > qend; --q) {
-      const int nb = (int)Ucnt[q];
-      TF acc0 = TF(0), acc1 = TF(0);
-      if (j < 4) {
-        int b = 1 + j;
-        for (; b + 4 < nb; b += 8) {
-          const TF* b0 = stg + (size_t)b * STR;
-          const TF* b1 = b0 + 4 * STR;
-          const TF* x0 = w + 7 * blk_col(b0);
-          const TF* x1 = w + 7 * blk_col(b1);
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) {
-            acc0 += b0[7 * c + mm] * x0[mm];
-            acc1 += b1[7 * c + mm] * x1[mm];
-          }
-        }
-        if (b < nb) {
-          const TF* b0 = stg + (size_t)b * STR;
-          const TF* x0 = w + 7 * blk_col(b0);
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) acc0 += b0[7 * c + mm] * x0[mm];
-        }
-      }
-      TF acc = acc0 + acc1;
-      acc += __shfl_down_sync(0xffffffffu, acc, 14);
-      acc += __shfl_down_sync(0xffffffffu, acc, 7);
+      const int nb = Ucnt[q];
+      const TF acc = row_dot<TF, STR>(stg, 1, nb, w, j, c);
       const TF t = (lane < 7) ? w[7 * q + lane] - acc : TF(0);
       TF tv[7];
 #pragma unroll
@@ -243,10 +251,17 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     if (lane == 0) atomicExch(err, 2);
     return;
   }
-  // restricted prolongation (R_i^0)^T: owned rows only
-  for (int idx = lane; idx < 7 * m; idx += 32) {
-    const int q = idx / 7, cc = idx - 7 * q;
-    if (R.owned[r0 + q]) z[7 * (int64_t)R.gnode[r0 + q] + cc] = (double)w[idx];
+  // restricted prolongation (R_i^0)^T: owned rows only, one row per lane
+  for (int q = lane; q < m; q += 32) {
+    if (R.owned[r0 + q]) {
+      const int64_t g7 = 7 * (int64_t)R.gnode[r0 + q];
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) z[g7 + cc] = (double)w[7 * q + cc];
+      if (z32) {
+#pragma unroll
+        for (int cc = 0; cc < 7; ++cc) z32[g7 + cc] = (float)w[7 * q + cc];
+      }
+    }
   }
 }
 
@@ -281,7 +296,8 @@ __global__ void k_pack_factors(int64_t nL, const int64_t* __restrict__ Lsrc, con
 
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r) {
-  return 128 + (size_t)NST * r.stage_blocks * Pack<TF>::stride * sizeof(TF) + (size_t)7 * r.max_rows * sizeof(TF);
+  return 128 + (size_t)r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) + (size_t)7 * r.max_rows * sizeof(TF) +
+         (size_t)4 * r.max_rows + 16 + (size_t)12 * r.max_groups;
 }
 
 template <class TF>
@@ -294,22 +310,28 @@ void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s) {
 }
 
 template <class TF>
-cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, int32_t* err,
-                                    cudaStream_t s) {
-  const size_t sm = ras_stream_smem<TF>(r);
-  cudaError_t e = cudaFuncSetAttribute(k_ras_apply_stream<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_ras_apply_stream<TF><<<r.np, 64, sm, s>>>(r, rin, z, err);
+cudaError_t ras_stream_init(const RasStreamDev& r) {
+  return cudaFuncSetAttribute(k_ras_apply_stream<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ras_stream_smem<TF>(r));
+}
+
+template <class TF>
+cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, float* z32, int32_t* err,
+                                    const int* guard, cudaStream_t s) {
+  k_ras_apply_stream<TF><<<r.np, 64, ras_stream_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
   return cudaGetLastError();
 }
+
+template cudaError_t ras_stream_init<float>(const RasStreamDev&);
+template cudaError_t ras_stream_init<double>(const RasStreamDev&);
 
 template size_t ras_stream_smem<float>(const RasStreamDev&);
 template size_t ras_stream_smem<double>(const RasStreamDev&);
 template void launch_pack_factors<float>(const RasStreamDev&, const float*, cudaStream_t);
 template void launch_pack_factors<double>(const RasStreamDev&, const double*, cudaStream_t);
-template cudaError_t launch_ras_apply_stream<float>(const RasStreamDev&, const double*, double*, int32_t*,
-                                                    cudaStream_t);
-template cudaError_t launch_ras_apply_stream<double>(const RasStreamDev&, const double*, double*, int32_t*,
-                                                     cudaStream_t);
+template cudaError_t launch_ras_apply_stream<float>(const RasStreamDev&, const double*, double*, float*, int32_t*,
+                                                    const int*, cudaStream_t);
+template cudaError_t launch_ras_apply_stream<double>(const RasStreamDev&, const double*, double*, float*, int32_t*,
+                                                     const int*, cudaStream_t);
 
 }  // namespace fsi

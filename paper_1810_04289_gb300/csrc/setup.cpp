@@ -111,7 +111,8 @@ static void rcb(const double* X, std::vector<int32_t>& idx, int64_t lo, int64_t 
 }
 
 RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t* node_problem,
-                  int32_t n_problems, int32_t np_req, int32_t overlap, int32_t fill_level) {
+                  int32_t n_problems, int32_t np_req, int32_t overlap, int32_t fill_level, int32_t ordering,
+                  const uint8_t* node_rank) {
   RasPlan R;
   // 1. non-overlapping partition: subdomains shared out over the problems by
   //    node count, then recursive coordinate bisection inside each problem
@@ -160,63 +161,73 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
       frontier = end;
     }
     const int64_t m = (int64_t)nodes.size();
-    // 3. reverse Cuthill-McKee order of the overlapped subgraph
+    // 3. order of the overlapped subdomain: natural (global node order), reverse
+    //    Cuthill-McKee, or reverse Cuthill-McKee with lumen nodes before wall nodes
     for (int64_t q = 0; q < m; ++q) loc[nodes[q]] = (int32_t)q;
-    std::vector<int32_t> degl(m, 0);
-    for (int64_t q = 0; q < m; ++q) {
-      int32_t v = nodes[q];
-      for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e)
-        if (loc[P.col[e]] >= 0 && P.col[e] != v) degl[q]++;
-    }
     std::vector<int32_t> order;
     order.reserve(m);
-    std::vector<uint8_t> seen(m, 0);
-    std::vector<int32_t> nb;
-    while ((int64_t)order.size() < m) {
-      // start from an unvisited node of minimum degree (a pseudo-peripheral choice)
-      int32_t st = -1;
-      for (int64_t q = 0; q < m; ++q)
-        if (!seen[q] && (st < 0 || degl[q] < degl[st])) st = (int32_t)q;
-      // one BFS sweep to move the start to the far end of the component
-      {
-        std::vector<int32_t> bfs{st};
-        std::vector<uint8_t> s2(m, 0);
-        s2[st] = 1;
-        for (size_t h = 0; h < bfs.size(); ++h) {
-          int32_t v = nodes[bfs[h]];
-          for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
-            int32_t w = loc[P.col[e]];
-            if (w >= 0 && !s2[w] && !seen[w]) {
-              s2[w] = 1;
-              bfs.push_back(w);
+    if (ordering == 0) {
+      for (int64_t q = 0; q < m; ++q) order.push_back((int32_t)q);
+      std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return nodes[a] < nodes[b]; });
+    } else {
+      std::vector<int32_t> degl(m, 0);
+      for (int64_t q = 0; q < m; ++q) {
+        int32_t v = nodes[q];
+        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e)
+          if (loc[P.col[e]] >= 0 && P.col[e] != v) degl[q]++;
+      }
+      std::vector<uint8_t> seen(m, 0);
+      std::vector<int32_t> nb;
+      while ((int64_t)order.size() < m) {
+        // start from an unvisited node of minimum degree (a pseudo-peripheral choice)
+        int32_t st = -1;
+        for (int64_t q = 0; q < m; ++q)
+          if (!seen[q] && (st < 0 || degl[q] < degl[st])) st = (int32_t)q;
+        // one BFS sweep to move the start to the far end of the component
+        {
+          std::vector<int32_t> bfs{st};
+          std::vector<uint8_t> s2(m, 0);
+          s2[st] = 1;
+          for (size_t h = 0; h < bfs.size(); ++h) {
+            int32_t v = nodes[bfs[h]];
+            for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+              int32_t w = loc[P.col[e]];
+              if (w >= 0 && !s2[w] && !seen[w]) {
+                s2[w] = 1;
+                bfs.push_back(w);
+              }
             }
           }
+          int32_t best = bfs.back();
+          // among the last BFS level pick the minimum degree node
+          st = best;
         }
-        int32_t best = bfs.back();
-        // among the last BFS level pick the minimum degree node
-        st = best;
-      }
-      seen[st] = 1;
-      size_t head = order.size();
-      order.push_back(st);
-      while (head < order.size()) {
-        int32_t q = order[head++];
-        int32_t v = nodes[q];
-        nb.clear();
-        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
-          int32_t w = loc[P.col[e]];
-          if (w >= 0 && !seen[w]) {
-            seen[w] = 1;
-            nb.push_back(w);
+        seen[st] = 1;
+        size_t head = order.size();
+        order.push_back(st);
+        while (head < order.size()) {
+          int32_t q = order[head++];
+          int32_t v = nodes[q];
+          nb.clear();
+          for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+            int32_t w = loc[P.col[e]];
+            if (w >= 0 && !seen[w]) {
+              seen[w] = 1;
+              nb.push_back(w);
+            }
           }
+          std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
+            return degl[a] < degl[b] || (degl[a] == degl[b] && nodes[a] < nodes[b]);
+          });
+          order.insert(order.end(), nb.begin(), nb.end());
         }
-        std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
-          return degl[a] < degl[b] || (degl[a] == degl[b] && nodes[a] < nodes[b]);
-        });
-        order.insert(order.end(), nb.begin(), nb.end());
+      }
+      std::reverse(order.begin(), order.end());
+      if (ordering == 2 && node_rank) {
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return node_rank[nodes[a]] < node_rank[nodes[b]]; });
       }
     }
-    std::reverse(order.begin(), order.end());
     std::vector<int32_t> perm(m);  // old local -> new local
     for (int64_t q = 0; q < m; ++q) perm[order[q]] = (int32_t)q;
     std::vector<int32_t> gn(m);

@@ -67,8 +67,11 @@ struct RasPlan {
 };
 
 // fill_level k: pattern of the level-of-fill ILU(k) of each J_i^delta (0 = the
-// pattern of J_i^delta itself).
+// pattern of J_i^delta itself). ordering of each subdomain: 0 natural (global
+// node order), 1 reverse Cuthill-McKee, 2 reverse Cuthill-McKee stably sorted
+// by node_rank (lumen nodes 0, interface 1, wall 2).
 RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n_nodes, const int32_t* node_problem,
-                  int32_t n_problems, int32_t np, int32_t overlap, int32_t fill_level);
+                  int32_t n_problems, int32_t np, int32_t overlap, int32_t fill_level, int32_t ordering,
+                  const uint8_t* node_rank);
 
 }  // namespace fsi

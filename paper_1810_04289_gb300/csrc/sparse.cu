@@ -20,35 +20,45 @@ inline int grid_for(int64_t work, int block) {
 
 // ---------------------------------------------------------------------------
 // SpMV: one warp per block row. Lane l < 28 owns output component r = l / 4 and
-// every fourth block (q = l % 4) of the row; its 7-term dot products run in the
-// value type T and accumulate in FP64; the four partial sums of a component are
-// combined by two shuffles. Lanes 28..31 idle.
+// every fourth block (q = l % 4) of the row; the four partial sums of a
+// component are combined by two shuffles. Lanes 28..31 idle. FP64: values,
+// vector and sums in FP64. Mixed: FP32 values and an FP32 copy of the vector,
+// sums in FP32, result stored in FP64 (no FP64 arithmetic in the loop).
 // ---------------------------------------------------------------------------
-template <class T>
+template <class TV, class TX>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __restrict__ row_ptr,
-                                                  const int32_t* __restrict__ col, const T* __restrict__ vals,
-                                                  const double* __restrict__ x, double* __restrict__ y) {
+                                                  const int32_t* __restrict__ col, const TV* __restrict__ vals,
+                                                  const TX* __restrict__ x, double* __restrict__ y,
+                                                  const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, q = lane & 3;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = warp0; row < n; row += nwarps) {
     const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
-    double acc = 0.0;
+    TX acc = TX(0);
     if (lane < 28) {
       for (int64_t b = b0 + q; b < b1; b += 4) {
-        const T* A = vals + 49 * b + 7 * r;
-        const double* xb = x + 7 * (int64_t)col[b];
-        T s = A[0] * T(xb[0]);
-#pragma unroll
-        for (int c = 1; c < 7; ++c) s += A[c] * T(xb[c]);
-        acc += (double)s;
+        const TV* A = vals + 49 * b + 7 * r;
+        const TX* xb = x + 7 * (int64_t)col[b];
+        TX s0 = TX(A[0]) * xb[0] + TX(A[1]) * xb[1];
+        TX s1 = TX(A[2]) * xb[2] + TX(A[3]) * xb[3];
+        TX s2 = TX(A[4]) * xb[4] + TX(A[5]) * xb[5];
+        acc += (s0 + s1) + (s2 + TX(A[6]) * xb[6]);
       }
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (lane < 28 && q == 0) y[7 * row + r] = acc;
+    if (lane < 28 && q == 0) y[7 * row + r] = (double)acc;
   }
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ y,
+                           const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -127,23 +137,29 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
   __syncwarp();
 }
 
-// Batched level-scheduled block ILU: grid = one CTA per subdomain (FW warps);
-// a warp factors one row of the current level with that row's blocks staged in
-// shared memory: for each L block (i,k) in column order it forms
-// A_ik <- A_ik D_k^{-1} and applies every update A_ij -= A_ik A_kj in one pass
-// (lane task = update x column), so each L block costs one round trip to the
-// finished rows k instead of one per update. Levels are separated by
-// __syncthreads.
+// Batched level-scheduled block ILU: grid = one CTA per subdomain (up to FW
+// warps); a warp factors one row of the current level entirely in its own
+// shared-memory slice: the row, the inverted pivots D_k of its L blocks and
+// every source block A_kj of its updates belong to finished rows, so they are
+// fetched together (one memory round trip per row); then for each L block
+// (i,k) in column order A_ik <- A_ik D_k^{-1} and all its updates
+// A_ij -= A_ik A_kj run from shared memory (lane task = update x column).
+// Levels are separated by __syncthreads.
 constexpr int FW = 4;
 
-template <class TF>
-__global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err,
-                                                        int32_t max_row_blocks) {
+// ALL = true: every source block of the row is fetched up front; false: the
+// sources of one L block at a time (rows too long for the whole set).
+template <class TF, bool ALL>
+__global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
-  TF* sAug = reinterpret_cast<TF*>(fsm) + warp * 98;
-  TF* sRow = reinterpret_cast<TF*>(fsm) + nw * 98 + (size_t)warp * max_row_blocks * 49;
+  const int32_t nsrc = ALL ? R.max_row_upd : R.max_entry_upd;
+  const size_t per = (size_t)(R.max_row_blocks + R.max_row_lent + nsrc) * 49 + 98;
+  TF* sRow = reinterpret_cast<TF*>(fsm) + (size_t)warp * per;
+  TF* sD = sRow + (size_t)R.max_row_blocks * 49;
+  TF* sSrc = sD + (size_t)R.max_row_lent * 49;
+  TF* sAug = sSrc + (size_t)nsrc * 49;
   const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s];
   for (int64_t l = R.sd_lvlL[s]; l < R.sd_lvlL[s + 1]; ++l) {
@@ -152,11 +168,31 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
       const int64_t q = r0 + R.lvlL_rows[ri];
       const int64_t rp = R.row_ptr[q];
       const int nblk = (int)(R.row_ptr[q + 1] - rp);
-      for (int e = lane; e < 49 * nblk; e += 32) sRow[e] = fac[49 * rp + e];
+      const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
+      const int64_t u0 = R.upd_ptr[e0], u1 = R.upd_ptr[e1];
+      const int nl = (int)(e1 - e0), nu = (int)(u1 - u0);
+      for (int idx = lane; idx < 49 * nblk; idx += 32) sRow[idx] = fac[49 * rp + idx];
+      for (int idx = lane; idx < 49 * nl; idx += 32) {
+        const int e = idx / 49;
+        sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
+      }
+      if (ALL)
+        for (int idx = lane; idx < 49 * nu; idx += 32) {
+          const int u = idx / 49;
+          sSrc[idx] = fac[49 * R.upd_src[u0 + u] + (idx - 49 * u)];
+        }
       __syncwarp();
-      for (int64_t e = R.lent_ptr[q]; e < R.lent_ptr[q + 1]; ++e) {
+      for (int64_t e = e0; e < e1; ++e) {
         TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
-        const TF* Dk = fac + 49 * R.lent_kdiag[e];
+        const TF* Dk = sD + 49 * (e - e0);
+        const int64_t us = ALL ? u0 : R.upd_ptr[e];
+        if (!ALL) {
+          const int ne = (int)(R.upd_ptr[e + 1] - us);
+          for (int idx = lane; idx < 49 * ne; idx += 32) {
+            const int u = idx / 49;
+            sSrc[idx] = fac[49 * R.upd_src[us + u] + (idx - 49 * u)];
+          }
+        }
         // A_ik <- A_ik D_k^{-1}
         TF v0 = TF(0), v1 = TF(0);
         {
@@ -164,7 +200,7 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
 #pragma unroll
           for (int mm = 0; mm < 7; ++mm) v0 += Aik[7 * r_0 + mm] * Dk[7 * mm + c_0];
           if (lane + 32 < 49) {
-            const int e1 = lane + 32, r_1 = e1 / 7, c_1 = e1 - 7 * r_1;
+            const int e1_ = lane + 32, r_1 = e1_ / 7, c_1 = e1_ - 7 * r_1;
 #pragma unroll
             for (int mm = 0; mm < 7; ++mm) v1 += Aik[7 * r_1 + mm] * Dk[7 * mm + c_1];
           }
@@ -174,12 +210,12 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
         if (lane + 32 < 49) Aik[lane + 32] = v1;
         __syncwarp();
         // A_ij -= A_ik A_kj for every update of this L block: task = (update, column)
-        const int64_t u0 = R.upd_ptr[e];
-        const int ntask = 7 * (int)(R.upd_ptr[e + 1] - u0);
+        const int64_t ub = R.upd_ptr[e];
+        const int ntask = 7 * (int)(R.upd_ptr[e + 1] - ub);
         for (int t = lane; t < ntask; t += 32) {
           const int u = t / 7, cc = t - 7 * u;
-          TF* Aij = sRow + 49 * (R.upd_tgt[u0 + u] - rp) + cc;
-          const TF* Akj = fac + 49 * R.upd_src[u0 + u] + cc;
+          TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
+          const TF* Akj = sSrc + 49 * (ub + u - us) + cc;
           TF col[7];
 #pragma unroll
           for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
@@ -194,7 +230,7 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
         __syncwarp();
       }
       warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
-      for (int e = lane; e < 49 * nblk; e += 32) fac[49 * rp + e] = sRow[e];
+      for (int idx = lane; idx < 49 * nblk; idx += 32) fac[49 * rp + idx] = sRow[idx];
       __syncwarp();
     }
     __syncthreads();
@@ -206,7 +242,9 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
 template <class TF>
 __global__ void __launch_bounds__(256) k_ras_apply(RasDev R, const TF* __restrict__ fac,
                                                    const double* __restrict__ rin, TF* __restrict__ work,
-                                                   double* __restrict__ z) {
+                                                   double* __restrict__ z, float* __restrict__ z32,
+                                                   const int* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s], m = R.sd_row[s + 1] - r0;
   const int grp = threadIdx.x >> 3, c = threadIdx.x & 7;
@@ -275,16 +313,23 @@ __global__ void __launch_bounds__(256) k_ras_apply(RasDev R, const TF* __restric
   for (int64_t idx = threadIdx.x; idx < 7 * m; idx += blockDim.x) {
     const int64_t q = idx / 7;
     const int cc = (int)(idx - 7 * q);
-    if (R.owned[r0 + q]) z[7 * (int64_t)R.gnode[r0 + q] + cc] = (double)w[idx];
+    if (R.owned[r0 + q]) {
+      z[7 * (int64_t)R.gnode[r0 + q] + cc] = (double)w[idx];
+      if (z32) z32[7 * (int64_t)R.gnode[r0 + q] + cc] = (float)w[idx];
+    }
   }
 }
 
 }  // namespace
 
-template <class T>
-void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const T* vals, const double* x,
-                     double* y, cudaStream_t s) {
-  k_bsr_spmv<T><<<grid_for(32 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y);
+template <class TV, class TX>
+void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const TV* vals, const TX* x,
+                     double* y, const int* guard, cudaStream_t s) {
+  k_bsr_spmv<TV, TX><<<grid_for(32 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y, guard);
+}
+
+void launch_to_float(int64_t n, const double* x, float* y, const int* guard, cudaStream_t s) {
+  k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, x, y, guard);
 }
 
 template <class TF, class TJ>
@@ -293,44 +338,57 @@ void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s
 }
 
 template <class TF>
-size_t ras_factor_smem_per_warp(int32_t max_row_blocks) {
-  return (size_t)98 * sizeof(TF) + (size_t)max_row_blocks * 49 * sizeof(TF);
+size_t ras_factor_smem_per_warp(const RasDev& r, bool all) {
+  return ((size_t)(r.max_row_blocks + r.max_row_lent + (all ? r.max_row_upd : r.max_entry_upd)) * 49 + 98) *
+         sizeof(TF);
 }
 
 // warps per factorisation CTA: up to FW, as many as the shared memory allows
+// (whole-row source prefetch whenever one warp's slice fits: one memory round
+// trip per row is worth more than extra warps waiting on a level barrier)
 template <class TF>
-int ras_factor_warps(int32_t max_row_blocks) {
-  const size_t per = ras_factor_smem_per_warp<TF>(max_row_blocks);
-  int nw = (int)((size_t)(220 * 1024) / per);
+int ras_factor_warps(const RasDev& r, bool* all_out) {
+  const size_t budget = 200 * 1024;
+  bool all = ras_factor_smem_per_warp<TF>(r, true) <= budget;
+  int nw = (int)(budget / ras_factor_smem_per_warp<TF>(r, all));
+  if (all_out) *all_out = all;
   return nw < 1 ? 0 : (nw > FW ? FW : nw);
 }
 
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
-  const int nw = ras_factor_warps<TF>(r.max_row_blocks);
-  const size_t sm = (size_t)nw * ras_factor_smem_per_warp<TF>(r.max_row_blocks);
-  cudaFuncSetAttribute(k_ras_factor<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_ras_factor<TF><<<r.np, 32 * nw, sm, s>>>(r, fac, err, r.max_row_blocks);
+  bool all = true;
+  const int nw = ras_factor_warps<TF>(r, &all);
+  const size_t sm = (size_t)nw * ras_factor_smem_per_warp<TF>(r, all);
+  if (all) {
+    cudaFuncSetAttribute(k_ras_factor<TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ras_factor<TF, true><<<r.np, 32 * nw, sm, s>>>(r, fac, err);
+  } else {
+    cudaFuncSetAttribute(k_ras_factor<TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ras_factor<TF, false><<<r.np, 32 * nw, sm, s>>>(r, fac, err);
+  }
 }
 
-template int ras_factor_warps<float>(int32_t);
-template int ras_factor_warps<double>(int32_t);
+template int ras_factor_warps<float>(const RasDev&, bool*);
+template int ras_factor_warps<double>(const RasDev&, bool*);
 
 template <class TF>
-void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, cudaStream_t s) {
-  k_ras_apply<TF><<<r.np, 256, 0, s>>>(r, fac, rin, work, z);
+void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,
+                      const int* guard, cudaStream_t s) {
+  k_ras_apply<TF><<<r.np, 256, 0, s>>>(r, fac, rin, work, z, z32, guard);
 }
 
-template void launch_bsr_spmv<double>(int64_t, const int64_t*, const int32_t*, const double*, const double*,
-                                      double*, cudaStream_t);
-template void launch_bsr_spmv<float>(int64_t, const int64_t*, const int32_t*, const float*, const double*,
-                                     double*, cudaStream_t);
+template void launch_bsr_spmv<double, double>(int64_t, const int64_t*, const int32_t*, const double*,
+                                              const double*, double*, const int*, cudaStream_t);
+template void launch_bsr_spmv<float, float>(int64_t, const int64_t*, const int32_t*, const float*, const float*,
+                                            double*, const int*, cudaStream_t);
 template void launch_ras_extract<double, double>(const RasDev&, const double*, double*, cudaStream_t);
 template void launch_ras_extract<float, float>(const RasDev&, const float*, float*, cudaStream_t);
 template void launch_ras_factor<double>(const RasDev&, double*, int32_t*, cudaStream_t);
 template void launch_ras_factor<float>(const RasDev&, float*, int32_t*, cudaStream_t);
-template void launch_ras_apply<double>(const RasDev&, const double*, const double*, double*, double*,
-                                       cudaStream_t);
-template void launch_ras_apply<float>(const RasDev&, const float*, const double*, float*, double*, cudaStream_t);
+template void launch_ras_apply<double>(const RasDev&, const double*, const double*, double*, double*, float*,
+                                       const int*, cudaStream_t);
+template void launch_ras_apply<float>(const RasDev&, const float*, const double*, float*, double*, float*,
+                                      const int*, cudaStream_t);
 
 }  // namespace fsi

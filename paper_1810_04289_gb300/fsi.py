@@ -47,7 +47,7 @@ class FsiOptions(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("n_subdomains", ctypes.c_int32), ("overlap", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("jac_lag", ctypes.c_int32), ("ilu_level", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
-                ("verbose", ctypes.c_int32)]
+                ("ordering", ctypes.c_int32), ("verbose", ctypes.c_int32)]
 
 
 class FsiSolveStats(ctypes.Structure):
@@ -60,7 +60,7 @@ class FsiStepStats(ctypes.Structure):
                 ("jacobian_evaluations", ctypes.c_int32), ("residual_evaluations", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double)] + \
                [(k, ctypes.c_double) for k in ("t_funceval", "t_jaceval", "t_pcsetup", "t_pcapply", "t_spmv",
-                                                "t_orth", "t_total")] + \
+                                                "t_orth", "t_total", "t_krylov")] + \
                [(k, ctypes.c_int32) for k in ("n_funceval", "n_jaceval", "n_pcsetup", "n_pcapply", "n_spmv",
                                                "n_orth")] + [("kernel_launches", ctypes.c_int64)]
 
