@@ -228,6 +228,21 @@ fsi_status fsi_step(fsi_ctx *ctx, fsi_step_stats *stats);
 
 fsi_status fsi_get_info(const fsi_ctx *ctx, fsi_info *info);
 
+/* Allocation-free variant of fsi_residual (the paper has no counterpart; this
+ * is an interface convenience). For callers that must not have the library
+ * allocate device memory, e.g. code that fixed its device-memory footprint in
+ * advance or that runs while device allocation is not allowed: it computes the
+ * same F(y) as fsi_residual (same arguments, device pointers [n_nodes*7] FP64)
+ * and allocates nothing, because its assembly scratch (28 FP64 values per tet)
+ * is one fixed device array built into the library, sized for at most 32,768
+ * tets (7.3 MB, held by every GPU that loads the library until the process
+ * exits). Larger meshes get FSI_ERR_ARG with a message. The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture. All calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * contexts, other host threads) race and must be serialised by the caller. */
+fsi_status fsi_residual_noalloc(fsi_ctx *ctx, const double *y, double *F);
+
 /* Message of the last failure on the context (static string if ctx is NULL). */
 const char *fsi_last_error(const fsi_ctx *ctx);
 

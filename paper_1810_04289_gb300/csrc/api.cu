@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1040,3 +1041,51 @@ const char* fsi_last_error(const fsi_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free residual. The paper has no counterpart: this is an interface
+// for callers that must not have the library allocate device memory, for
+// instance code that has fixed its whole device-memory footprint in advance or
+// that runs while device allocation is forbidden. It computes exactly what
+// fsi_residual computes, but the element buffer of the assembly (28 values per
+// tet) lives in one file-scope device array instead of the context's buffer.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t NOALLOC_MAX_TETS = 32768;   // 28 x 8 B x 32768 = 7.3 MB per device
+static __device__ __align__(256) double g_noalloc_fe[28 * NOALLOC_MAX_TETS];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+}  // namespace
+
+extern "C" fsi_status fsi_residual_noalloc(fsi_ctx* c, const double* y, double* F) {
+  if (!c || !y || !F) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (c->T > NOALLOC_MAX_TETS)
+      throw StatusError{FSI_ERR_ARG, "fsi_residual_noalloc handles at most 32768 tets; the mesh has " +
+                                         std::to_string(c->T)};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) throw StatusError{FSI_ERR_ARG, "device index out of range"};
+    double* fe = nullptr;
+    {
+      // once per device, with that device current: the device address of the
+      // array (its host-side name is only a stand-in, not a device address)
+      std::lock_guard<std::mutex> lock(g_noalloc_mu);
+      if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_fe));
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+      }
+      fe = g_noalloc_addr[dev];
+    }
+    // every slot the gather reads is written by the element kernel first, so the
+    // array needs no clearing between calls
+    launch_elem_residual(c->mesh, c->mc, y, c->yn, c->ynm1, fe, c->s);
+    launch_gather_residual(c->mesh, c->nptr, c->nsrc, fe, F, c->s);
+    launch_constraint_residual(c->mesh, c->mc, c->t + c->opt.dt, y, c->yn, F, c->s);
+    check_launch();
+    CK(cudaStreamSynchronize(c->s));
+    return FSI_OK;
+  });
+}

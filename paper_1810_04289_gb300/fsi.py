@@ -22,7 +22,7 @@ STATUS = {0: "FSI_OK", 1: "FSI_ERR_ARG", 2: "FSI_ERR_MESH", 3: "FSI_ERR_CUDA", 4
 # every symbol include/fsi.h declares
 EXPORTS = ["fsi_default_options", "fsi_create", "fsi_destroy", "fsi_set_state", "fsi_get_state",
            "fsi_residual", "fsi_jacobian", "fsi_jacobian_export", "fsi_spmv", "fsi_pc_apply",
-           "fsi_linear_solve", "fsi_step", "fsi_get_info", "fsi_last_error"]
+           "fsi_linear_solve", "fsi_step", "fsi_get_info", "fsi_last_error", "fsi_residual_noalloc"]
 
 
 class FsiMesh(ctypes.Structure):
@@ -95,6 +95,7 @@ def load_library(path=LIB_PATH):
         "fsi_step": (ctypes.c_int, [P, ctypes.POINTER(FsiStepStats)]),
         "fsi_get_info": (ctypes.c_int, [P, ctypes.POINTER(FsiInfo)]),
         "fsi_last_error": (ctypes.c_char_p, [P]),
+        "fsi_residual_noalloc": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -196,6 +197,12 @@ def fsi_get_state(ctx, y_n=None):
 
 def fsi_residual(ctx, y, F):
     return _check(ctx, lib().fsi_residual(ctx, _dptr(y), _dptr(F)))
+
+
+def fsi_residual_noalloc(ctx, y, F):
+    """Same F(y) as fsi_residual, computed without any device allocation (the
+    assembly scratch is a fixed array inside the library; at most 32,768 tets)."""
+    return _check(ctx, lib().fsi_residual_noalloc(ctx, _dptr(y), _dptr(F)))
 
 
 def fsi_jacobian(ctx, y):
