@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="tube-96x32x15", choices=sorted(WORKLOADS))
-    p.add_argument("--subdomains", type=int, default=64)
+    p.add_argument("--subdomains", type=int, default=256)
     p.add_argument("--ilu", type=int, default=1)
     p.add_argument("--overlap", type=int, default=1)
     p.add_argument("--newton-rtol", type=float, default=1e-6)

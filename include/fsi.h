@@ -163,7 +163,8 @@ typedef struct {
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,
  * newton_maxit 20, gmres_restart 30, gmres_maxit 1000, n_subdomains 64,
  * overlap 1, precision 0, jac_lag 1, ilu_level 1 (the paper's default subdomain
- * solver, Sec. 4), threads_per_row 0, ordering 0. A negative ilu_level or overlap in the
+ * solver, Sec. 4), threads_per_row 0, ordering 1 (RCM, the paper's default,
+ * Sec. 4.5). A negative ilu_level or overlap in the
  * caller's options also selects the default. */
 void fsi_default_options(fsi_options *opts);
 

@@ -433,7 +433,7 @@ void fill_defaults(fsi_options* o) {
   o->jac_lag = 1;
   o->ilu_level = 1;
   o->threads_per_row = 0;
-  o->ordering = 0;
+  o->ordering = 1;
   o->verbose = 0;
 }
 
@@ -714,7 +714,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Ucol = cp->upload(Ucol);
       // stage geometry: FSI_STAGE_BLOCKS / FSI_STAGES override the defaults (tuning)
       int64_t sbdef = cp->mixed ? 128 : 64;
-      int nst = 4;
+      int nst = 2;
       if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) sbdef = std::max(1, std::atoi(e));
       if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));
       const int64_t SB = std::max<int64_t>(maxblk, sbdef);
