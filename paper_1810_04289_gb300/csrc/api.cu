@@ -64,6 +64,8 @@ struct fsi_ctx {
   int32_t *nsrc = nullptr, *bsrc = nullptr;
   double* Fe = nullptr;
   void* Ke = nullptr;
+  void* Xl = nullptr;         // per-tet local reference coordinates, Jacobian type
+  float* y32 = nullptr;       // mixed: FP32 copies of y, y_n, y_{n-1} for the Jacobian
   int64_t* row_ptr = nullptr;
   int32_t* col = nullptr;
   int32_t* diag = nullptr;
@@ -215,11 +217,14 @@ void jacobian(fsi_ctx* c, const double* y) {
   c->launches += 3;
   int h = c->begin_phase(PH_JAC);
   if (c->mixed) {
-    launch_elem_jacobian<float>(c->mesh, c->mc, y, c->yn, c->ynm1, (float*)c->Ke, c->s);
+    c->launches += 1;
+    launch_states_to_float(c->n, y, c->yn, c->ynm1, c->y32, c->s);
+    launch_elem_jacobian<float>(c->mesh, c->mc, (const float*)c->Xl, c->y32, c->y32 + c->n, c->y32 + 2 * c->n,
+                                (float*)c->Ke, c->s);
     launch_gather_jacobian<float>(c->nnzb, c->bptr, c->bsrc, (const float*)c->Ke, (float*)c->vals, c->s);
     launch_constraint_jacobian<float>(c->mesh, c->mc, c->diag, (float*)c->vals, c->s);
   } else {
-    launch_elem_jacobian<double>(c->mesh, c->mc, y, c->yn, c->ynm1, (double*)c->Ke, c->s);
+    launch_elem_jacobian<double>(c->mesh, c->mc, (const double*)c->Xl, y, c->yn, c->ynm1, (double*)c->Ke, c->s);
     launch_gather_jacobian<double>(c->nnzb, c->bptr, c->bsrc, (const double*)c->Ke, (double*)c->vals, c->s);
     launch_constraint_jacobian<double>(c->mesh, c->mc, c->diag, (double*)c->vals, c->s);
   }
@@ -586,6 +591,20 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->diag = cp->upload(P.diag);
     const size_t vs = cp->mixed ? sizeof(float) : sizeof(double);
     cp->Fe = cp->dalloc<double>(28 * T0);
+    {
+      std::vector<double> xl(12 * T0);
+      for (int64_t t = 0; t < T0; ++t)
+        for (int a = 0; a < 4; ++a)
+          for (int i = 0; i < 3; ++i)
+            xl[12 * t + 3 * a + i] = mesh->X[3 * (int64_t)tets[4 * t + a] + i] - mesh->X[3 * (int64_t)tets[4 * t] + i];
+      if (cp->mixed) {
+        std::vector<float> xf(xl.begin(), xl.end());
+        cp->Xl = cp->upload(xf);
+        cp->y32 = cp->dalloc<float>(3 * 7 * N);
+      } else {
+        cp->Xl = cp->upload(xl);
+      }
+    }
     cp->Ke = cp->dalloc<char>((int64_t)(784 * vs) * T0);
     cp->vals = cp->dalloc<char>((int64_t)(49 * vs) * cp->nnzb);
     CK(cudaMemsetAsync(cp->vals, 0, 49 * vs * cp->nnzb, cp->s));
@@ -713,7 +732,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
       // stage geometry: FSI_STAGE_BLOCKS / FSI_STAGES override the defaults (tuning)
-      int64_t sbdef = cp->mixed ? 128 : 64;
+      int64_t sbdef = cp->mixed ? 64 : 32;
       int nst = 2;
       if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) sbdef = std::max(1, std::atoi(e));
       if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));

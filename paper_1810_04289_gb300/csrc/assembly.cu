@@ -149,13 +149,16 @@ __global__ void k_constraint_residual(MeshDev m, MatConst mc, double t, const do
 }
 
 // One Jacobian column per thread: 28 threads per tet (column = node b, dof k),
-// forward-mode derivative of the element residual along that column.
+// forward-mode derivative of the element residual along that column. Inputs
+// are already in the arithmetic type T: per-tet reference coordinates relative
+// to vertex 0 (Xl, 12 per tet) and node states (y, y_old, y_older), so the FP32
+// kernel runs no FP64 instruction.
 constexpr int JAC_TETS_PER_BLOCK = 8;
 
 template <class T>
 __global__ void __launch_bounds__(28 * JAC_TETS_PER_BLOCK)
-k_elem_jacobian(MeshDev m, MatConst mc, const double* __restrict__ y, const double* __restrict__ y1,
-                const double* __restrict__ y2, T* __restrict__ Ke) {
+k_elem_jacobian(MeshDev m, MatConst mc, const T* __restrict__ Xl, const T* __restrict__ y,
+                const T* __restrict__ y1, const T* __restrict__ y2, T* __restrict__ Ke) {
   const int tl = threadIdx.x / 28;
   const int colid = threadIdx.x - 28 * tl;
   const int b = colid / 7, k = colid - 7 * (colid / 7);
@@ -164,27 +167,30 @@ k_elem_jacobian(MeshDev m, MatConst mc, const double* __restrict__ y, const doub
     int n[4];
     uint32_t f[4];
     load_tet(m, t, n, f);
-    T Xl[4][3];
-    load_X<T>(m, n, Xl);
+    T X[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) X[a][i] = Xl[12 * t + 3 * a + i];
     T out[4][7];
     if (t < m.Tf) {
       Dual<T> u[4][3], p[4], d[4][3];
       T u1[4][3], d1[4][3];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const double* ya = y + 7 * (int64_t)n[a];
-        const double* y1a = y1 + 7 * (int64_t)n[a];
+        const T* ya = y + 7 * (int64_t)n[a];
+        const T* y1a = y1 + 7 * (int64_t)n[a];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          u[a][i] = Dual<T>(T(ya[i]), (a == b && k == i) ? T(1) : T(0));
-          d[a][i] = Dual<T>(T(ya[4 + i]), (a == b && k == 4 + i) ? T(1) : T(0));
-          u1[a][i] = T(y1a[i]);
-          d1[a][i] = T(y1a[4 + i]);
+          u[a][i] = Dual<T>(ya[i], (a == b && k == i) ? T(1) : T(0));
+          d[a][i] = Dual<T>(ya[4 + i], (a == b && k == 4 + i) ? T(1) : T(0));
+          u1[a][i] = y1a[i];
+          d1[a][i] = y1a[4 + i];
         }
-        p[a] = Dual<T>(T(ya[3]), (a == b && k == 3) ? T(1) : T(0));
+        p[a] = Dual<T>(ya[3], (a == b && k == 3) ? T(1) : T(0));
       }
       Dual<T> Rm[4][3], Rc[4], Rh[4][3];
-      fluid_element<Dual<T>, T>(Xl, u, p, d, u1, d1, mc, Rm, Rc, Rh);
+      fluid_element<Dual<T>, T>(X, u, p, d, u1, d1, mc, Rm, Rc, Rh);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const bool uc = f[a] & NF_U_CONSTR, pc = f[a] & NF_P_IDENT, dz = f[a] & NF_D_ZERO, itf = f[a] & NF_ITF;
@@ -207,12 +213,12 @@ k_elem_jacobian(MeshDev m, MatConst mc, const double* __restrict__ y, const doub
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            d[a][i] = Dual<T>(T(y[7 * (int64_t)n[a] + 4 + i]), (a == b && k == 4 + i) ? T(1) : T(0));
-            d1[a][i] = T(y1[7 * (int64_t)n[a] + 4 + i]);
-            d2[a][i] = T(y2[7 * (int64_t)n[a] + 4 + i]);
+            d[a][i] = Dual<T>(y[7 * (int64_t)n[a] + 4 + i], (a == b && k == 4 + i) ? T(1) : T(0));
+            d1[a][i] = y1[7 * (int64_t)n[a] + 4 + i];
+            d2[a][i] = y2[7 * (int64_t)n[a] + 4 + i];
           }
         Dual<T> Rw[4][3];
-        wall_element<Dual<T>, T>(Xl, d, d1, d2, mc, Rw);
+        wall_element<Dual<T>, T>(X, d, d1, d2, mc, Rw);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const bool dz = f[a] & NF_D_ZERO;
@@ -227,6 +233,15 @@ k_elem_jacobian(MeshDev m, MatConst mc, const double* __restrict__ y, const doub
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int r = 0; r < 7; ++r) o[196 * a + 7 * r] = out[a][r];
+  }
+}
+
+__global__ void k_states_to_float(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                  const double* __restrict__ c, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = (float)a[i];
+    out[n + i] = (float)b[i];
+    out[2 * n + i] = (float)c[i];
   }
 }
 
@@ -283,12 +298,17 @@ void launch_constraint_residual(const MeshDev& m, const MatConst& mc, double t, 
 }
 
 template <class T>
-void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const double* y, const double* y1,
-                          const double* y2, T* Ke, cudaStream_t s) {
+void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const T* Xl, const T* y, const T* y1, const T* y2,
+                          T* Ke, cudaStream_t s) {
   if (m.T == 0) return;
   int64_t blocks = (m.T + JAC_TETS_PER_BLOCK - 1) / JAC_TETS_PER_BLOCK;
   if (blocks > 152 * 256) blocks = 152 * 256;
-  k_elem_jacobian<T><<<(int)blocks, 28 * JAC_TETS_PER_BLOCK, 0, s>>>(m, mc, y, y1, y2, Ke);
+  k_elem_jacobian<T><<<(int)blocks, 28 * JAC_TETS_PER_BLOCK, 0, s>>>(m, mc, Xl, y, y1, y2, Ke);
+}
+
+void launch_states_to_float(int64_t n, const double* a, const double* b, const double* c, float* out,
+                            cudaStream_t s) {
+  k_states_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, a, b, c, out);
 }
 
 template <class T>
@@ -304,9 +324,9 @@ void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int3
 }
 
 template void launch_elem_jacobian<double>(const MeshDev&, const MatConst&, const double*, const double*,
-                                           const double*, double*, cudaStream_t);
-template void launch_elem_jacobian<float>(const MeshDev&, const MatConst&, const double*, const double*,
-                                          const double*, float*, cudaStream_t);
+                                           const double*, const double*, double*, cudaStream_t);
+template void launch_elem_jacobian<float>(const MeshDev&, const MatConst&, const float*, const float*,
+                                          const float*, const float*, float*, cudaStream_t);
 template void launch_gather_jacobian<double>(int64_t, const int64_t*, const int32_t*, const double*, double*,
                                              cudaStream_t);
 template void launch_gather_jacobian<float>(int64_t, const int64_t*, const int32_t*, const float*, float*,

@@ -27,9 +27,14 @@ void launch_gather_residual(const MeshDev& m, const int64_t* nptr, const int32_t
                             double* F, cudaStream_t s);
 void launch_constraint_residual(const MeshDev& m, const MatConst& mc, double t, const double* y,
                                 const double* y1, double* F, cudaStream_t s);
+// Xl: per-tet reference coordinates relative to vertex 0 (12 per tet); y, y1, y2
+// node states, all in the arithmetic type T
 template <class T>
-void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const double* y, const double* y1,
-                          const double* y2, T* Ke, cudaStream_t s);
+void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const T* Xl, const T* y, const T* y1, const T* y2,
+                          T* Ke, cudaStream_t s);
+// out = [a | b | c] converted to FP32 (3 n floats)
+void launch_states_to_float(int64_t n, const double* a, const double* b, const double* c, float* out,
+                            cudaStream_t s);
 template <class T>
 void launch_gather_jacobian(int64_t nnzb, const int64_t* bptr, const int32_t* bsrc, const T* Ke, T* vals,
                             cudaStream_t s);

@@ -237,6 +237,77 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
   }
 }
 
+// Batched block ILU, whole CTA on one row: one CTA per subdomain walks its rows
+// in increasing order (a topological order of the elimination). The row, the
+// inverted pivots of its L blocks and all source blocks of its updates belong
+// to finished rows and are fetched into shared memory in one round trip; then
+// for each L block (i,k): threads 0..48 form A_ik D_k^{-1} into a separate
+// buffer (and the row), and all threads apply the block's updates
+// A_ij -= A_ik A_kj (task = update x column) - two barriers per L block.
+template <class TF>
+__global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict__ fac, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  TF* sRow = reinterpret_cast<TF*>(fsm);
+  TF* sD = sRow + (size_t)R.max_row_blocks * 49;
+  TF* sSrc = sD + (size_t)R.max_row_lent * 49;
+  TF* sScl = sSrc + (size_t)R.max_row_upd * 49;
+  TF* sAug = sScl + 49;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int s = blockIdx.x;
+  for (int64_t q = R.sd_row[s]; q < R.sd_row[s + 1]; ++q) {
+    const int64_t rp = R.row_ptr[q];
+    const int nblk = (int)(R.row_ptr[q + 1] - rp);
+    const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
+    const int64_t u0 = R.upd_ptr[e0], u1 = R.upd_ptr[e1];
+    const int nl = (int)(e1 - e0), nu = (int)(u1 - u0);
+    for (int idx = tid; idx < 49 * nblk; idx += nt) sRow[idx] = fac[49 * rp + idx];
+    for (int idx = tid; idx < 49 * nl; idx += nt) {
+      const int e = idx / 49;
+      sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
+    }
+    for (int idx = tid; idx < 49 * nu; idx += nt) {
+      const int u = idx / 49;
+      sSrc[idx] = fac[49 * R.upd_src[u0 + u] + (idx - 49 * u)];
+    }
+    __syncthreads();
+    for (int64_t e = e0; e < e1; ++e) {
+      TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
+      if (tid < 49) {
+        const TF* Dk = sD + 49 * (e - e0);
+        const int r = tid / 7, c = tid - 7 * r;
+        TF v = TF(0);
+#pragma unroll
+        for (int mm = 0; mm < 7; ++mm) v += Aik[7 * r + mm] * Dk[7 * mm + c];
+        sScl[tid] = v;
+      }
+      __syncthreads();
+      if (tid < 49) Aik[tid] = sScl[tid];
+      const int64_t ub = R.upd_ptr[e];
+      const int ntask = 7 * (int)(R.upd_ptr[e + 1] - ub);
+      for (int t = tid; t < ntask; t += nt) {
+        const int u = t / 7, cc = t - 7 * u;
+        TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
+        const TF* Akj = sSrc + 49 * (ub + u - u0) + cc;
+        TF col[7];
+#pragma unroll
+        for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
+#pragma unroll
+        for (int rr = 0; rr < 7; ++rr) {
+          TF acc = Aij[7 * rr];
+#pragma unroll
+          for (int mm = 0; mm < 7; ++mm) acc -= sScl[7 * rr + mm] * col[mm];
+          Aij[7 * rr] = acc;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < 32) warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
+    __syncthreads();
+    for (int idx = tid; idx < 49 * nblk; idx += nt) fac[49 * rp + idx] = sRow[idx];
+    __syncthreads();
+  }
+}
+
 // Batched RAS apply: grid = one CTA per subdomain; 8-lane groups own one row
 // (lane c < 7 computes component c). work holds the subdomain vector.
 template <class TF>
@@ -356,7 +427,18 @@ int ras_factor_warps(const RasDev& r, bool* all_out) {
 }
 
 template <class TF>
+size_t ras_factor_cta_smem(const RasDev& r) {
+  return ((size_t)(r.max_row_blocks + r.max_row_lent + r.max_row_upd + 1) * 49 + 98) * sizeof(TF);
+}
+
+template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
+  const size_t smc = ras_factor_cta_smem<TF>(r);
+  if (smc <= 200 * 1024) {
+    cudaFuncSetAttribute(k_ras_factor_cta<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    k_ras_factor_cta<TF><<<r.np, 256, smc, s>>>(r, fac, err);
+    return;
+  }
   bool all = true;
   const int nw = ras_factor_warps<TF>(r, &all);
   const size_t sm = (size_t)nw * ras_factor_smem_per_warp<TF>(r, all);

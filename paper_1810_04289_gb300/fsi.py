@@ -290,6 +290,8 @@ class Solver:
         t = self.torch
         if a is None:
             return t.zeros((self.N, 7), dtype=t.float64, device="cuda")
+        if isinstance(a, t.Tensor):
+            return a.to(device="cuda", dtype=t.float64).reshape(self.N, 7).contiguous()
         return t.as_tensor(np.asarray(a, dtype=np.float64), device="cuda").reshape(self.N, 7).contiguous()
 
     def set_state(self, y_n, y_nm1=None, y_nm2=None, t=0.0):
