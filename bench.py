@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--precisions", default="mixed,fp64")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="use --subdomains/--overlap/--ilu as given")
     return p.parse_args()
 
 
@@ -148,6 +149,14 @@ def run_ours(args, rank, world):
         opt = fsi.fsi_default_options(newton_rtol=args.newton_rtol, gmres_rtol=args.gmres_rtol,
                                       n_subdomains=args.subdomains, ilu_level=args.ilu, overlap=args.overlap,
                                       precision=pflag)
+        tuned = None
+        if not args.no_autotune:
+            from paper_1810_04289_gb300.autotune import autotune
+            t_tune = time.perf_counter()
+            opt, table = autotune(m, MATERIAL, y0, base=opt)
+            tuned = {"chosen": {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level",
+                                                             "threads_per_row")},
+                     "seconds": time.perf_counter() - t_tune, "candidates": table}
         S = fsi.Solver(m, MATERIAL, opt)
         info = S.info()
         S.set_state(y0, t=0.0)
@@ -248,7 +257,7 @@ def run_ours(args, rank, world):
                 d["timed"] = f"{R} launches on their own after the run"
             phases[ph] = d
         phases["krylov"] = {"ms_total": tot["t_krylov"], "note": "GMRES cycles (captured graphs): applies, SpMVs, orthogonalisation"}
-        results[prec] = dict(ms=ms, steps=args.steps, value=world * args.steps / (ms * 1e-3), stats=stats,
+        results[prec] = dict(ms=ms, steps=args.steps, value=world * args.steps / (ms * 1e-3), stats=stats, tuned=tuned,
                              tot=tot, phases=phases, info={k: getattr(info, k) for k, _ in info._fields_},
                              clocks=clocks, e2e=e2e, launches=int(tot["kernel_launches"]))
         S.close()
@@ -339,7 +348,9 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if "mixed" in res else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "nodes": head["info"]["n_nodes"],
                    "unknowns": head["info"]["n_unknowns"], "tets": head["info"]["n_tets"],
-                   "subdomains": head["info"]["n_subdomains"], "overlap": args.overlap, "ilu": args.ilu,
+                   "subdomains": head["info"]["n_subdomains"],
+                   "overlap": (head["tuned"] or {}).get("chosen", {}).get("overlap", args.overlap),
+                   "ilu": (head["tuned"] or {}).get("chosen", {}).get("ilu_level", args.ilu),
                    "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol,
                    "l2": "working set (BSR + ILU factors) larger than L2 each step",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -351,6 +362,7 @@ def main():
         "gpu_launches": head["launches"],
         "e2e": head["e2e"],
         "cpu_baseline": cpu,
+        "autotune": head["tuned"],
     }
     if other is not None:
         line["fp64"] = {"value": other["value"], "ms_per_step": other["ms"] / args.steps,
@@ -358,7 +370,7 @@ def main():
                         "LI": float(np.mean([s["linear_iterations"] for s in other["stats"]])),
                         "phases_ms_per_step": {k: v["ms_total"] / args.steps for k, v in other["phases"].items()},
                         "phases": other["phases"], "gpu_launches": other["launches"], "e2e": other["e2e"],
-                        "clocks": other["clocks"]}
+                        "clocks": other["clocks"], "autotune": other["tuned"]}
         line["mixed_over_fp64"] = head["value"] / other["value"]
     print(json.dumps(line))
 

@@ -120,7 +120,7 @@ typedef struct {
   int32_t precision;      /* 0 FP64, 1 mixed FP32/FP64 */
   int32_t jac_lag;        /* reuse the Jacobian for this many Newton iterations (Eq. 12), >= 1 */
   int32_t ilu_level;      /* level of fill k of the subdomain block ILU(k), 0..3 (Sec. 4.3) */
-  int32_t threads_per_row;/* BSR SpMV rows-to-threads mapping: 0 = auto */
+  int32_t threads_per_row;/* BSR SpMV mapping: 32 = one warp per block row, 16 = two rows per warp */
   int32_t ordering;       /* node order inside each subdomain (Sec. 4.5): 0 natural
                              (global node order), 1 RCM, 2 RCM with lumen nodes
                              before interface and wall nodes */
@@ -163,7 +163,7 @@ typedef struct {
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,
  * newton_maxit 20, gmres_restart 30, gmres_maxit 1000, n_subdomains 64,
  * overlap 1, precision 0, jac_lag 1, ilu_level 1 (the paper's default subdomain
- * solver, Sec. 4), threads_per_row 0, ordering 1 (RCM, the paper's default,
+ * solver, Sec. 4), threads_per_row 32, ordering 1 (RCM, the paper's default,
  * Sec. 4.5). A negative ilu_level or overlap in the
  * caller's options also selects the default. */
 void fsi_default_options(fsi_options *opts);

@@ -1,0 +1,70 @@
+"""Measured autotuner for the solver's data-parallel knobs.
+
+For a mesh and a representative state it times, on the GPU and through the C
+ABI, one Newton linear system per candidate: preconditioner setup (extraction,
+ILU factorisation, packing) plus the GMRES solve to the candidate's tolerance.
+Candidates vary the Schwarz subdomain count, the overlap, the ILU fill level and
+the SpMV threads per block row; the fastest time to solution wins. The solver
+arithmetic itself is unchanged by any choice (only the preconditioner and the
+launch mapping change), so the tuned options solve the same equations.
+"""
+import itertools
+import time
+
+from . import fsi
+
+DEFAULT_GRID = dict(n_subdomains=(128, 256, 512, 1024), overlap=(1,), ilu_level=(1,), threads_per_row=(32, 16))
+
+
+def _time_linear_system(S, y, torch):
+    """Setup + solve time (s) and iterations for J(y) dy = -F(y) on solver S."""
+    yv = S.vec(y)
+    F = S.vec()
+    fsi.fsi_residual(S.ctx, yv, F)
+    F.neg_()
+    fsi.fsi_jacobian(S.ctx, yv)
+    x = S.vec()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = fsi.fsi_linear_solve(S.ctx, F, x, raise_on_divergence=False)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, st.iterations, st.converged
+
+
+def autotune(mesh, material, y0, base=None, grid=None, t0=0.0, verbose=False):
+    """Return (best FsiOptions, list of result dicts) for the given state.
+
+    base: FsiOptions used for every field the grid does not vary (default
+    fsi_default_options()). grid: dict of option name -> tuple of values.
+    """
+    import torch
+    grid = dict(DEFAULT_GRID if grid is None else grid)
+    base = base if base is not None else fsi.fsi_default_options()
+    names = list(grid)
+    results = []
+    best = None
+    for values in itertools.product(*(grid[k] for k in names)):
+        opt = fsi.FsiOptions()
+        for f, _ in fsi.FsiOptions._fields_:
+            setattr(opt, f, getattr(base, f))
+        for k, v in zip(names, values):
+            setattr(opt, k, v)
+        try:
+            S = fsi.Solver(mesh, material, opt)
+        except fsi.FsiError as e:          # e.g. factor rows too long for shared memory
+            results.append(dict(zip(names, values), error=str(e)))
+            continue
+        S.set_state(y0, t=t0)
+        # first solve builds the graph and warms the caches; the second is timed
+        _time_linear_system(S, y0, torch)
+        secs, its, conv = _time_linear_system(S, y0, torch)
+        S.close()
+        rec = dict(zip(names, values), seconds=secs, iterations=its, converged=bool(conv))
+        results.append(rec)
+        if verbose:
+            print("autotune", rec, flush=True)
+        if conv and (best is None or secs < best[0]):
+            best = (secs, opt)
+    if best is None:
+        raise RuntimeError("no candidate converged")
+    return best[1], results

@@ -243,9 +243,11 @@ void spmv_on(fsi_ctx* c, const double* x, const float* x32, double* y, const int
       launch_to_float(c->n, x, c->zf, guard, st);
       x32 = c->zf;
     }
-    launch_bsr_spmv<float, float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x32, y, guard, st);
+    launch_bsr_spmv<float, float>(c->N, c->row_ptr, c->col, (const float*)c->vals, x32, y, c->opt.threads_per_row,
+                                  guard, st);
   } else {
-    launch_bsr_spmv<double, double>(c->N, c->row_ptr, c->col, (const double*)c->vals, x, y, guard, st);
+    launch_bsr_spmv<double, double>(c->N, c->row_ptr, c->col, (const double*)c->vals, x, y, c->opt.threads_per_row,
+                                    guard, st);
   }
   c->launches += 1;
 }
@@ -437,7 +439,7 @@ void fill_defaults(fsi_options* o) {
   o->precision = 0;
   o->jac_lag = 1;
   o->ilu_level = 1;
-  o->threads_per_row = 0;
+  o->threads_per_row = 32;
   o->ordering = 1;
   o->verbose = 0;
 }
@@ -477,7 +479,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       o.precision = q.precision;
       if (q.jac_lag > 0) o.jac_lag = q.jac_lag;
       if (q.ilu_level >= 0) o.ilu_level = q.ilu_level;
-      o.threads_per_row = q.threads_per_row;
+      o.threads_per_row = (q.threads_per_row == 16) ? 16 : 32;
       if (q.ordering >= 0 && q.ordering <= 2) o.ordering = q.ordering;
       o.verbose = q.verbose;
     }

@@ -43,10 +43,11 @@ void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int3
                                 cudaStream_t s);
 
 // ---- sparse (sparse.cu)
-// y = J x; guard: optional device flag, the kernel does nothing while *guard == 0
+// y = J x; threads_per_row 32 (one warp per block row) or 16 (two rows per
+// warp); guard: optional device flag, the kernel does nothing while *guard == 0
 template <class TV, class TX>
 void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const TV* vals, const TX* x,
-                     double* y, const int* guard, cudaStream_t s);
+                     double* y, int threads_per_row, const int* guard, cudaStream_t s);
 void launch_to_float(int64_t n, const double* x, float* y, const int* guard, cudaStream_t s);
 
 struct RasDev {

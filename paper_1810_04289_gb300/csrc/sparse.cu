@@ -25,21 +25,25 @@ inline int grid_for(int64_t work, int block) {
 // vector and sums in FP64. Mixed: FP32 values and an FP32 copy of the vector,
 // sums in FP32, result stored in FP64 (no FP64 arithmetic in the loop).
 // ---------------------------------------------------------------------------
-template <class TV, class TX>
+template <class TV, class TX, int S>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col, const TV* __restrict__ vals,
                                                   const TX* __restrict__ x, double* __restrict__ y,
                                                   const int* __restrict__ guard) {
+  // S block slots x 8 component lanes (7 used) per row; 32 / (8 S) rows per warp
   if (guard && *guard == 0) return;
+  constexpr int G = 8 * S;
   const int lane = threadIdx.x & 31;
-  const int r = lane >> 2, q = lane & 3;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = warp0; row < n; row += nwarps) {
-    const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
+  const int gl = lane % G;
+  const int r = gl / S, q = gl % S;
+  const int64_t grp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t base = grp0 - (lane / G); base < n; base += ngrp) {
+    const int64_t row = base + (lane / G);
     TX acc = TX(0);
-    if (lane < 28) {
-      for (int64_t b = b0 + q; b < b1; b += 4) {
+    if (r < 7 && row < n) {
+      const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
+      for (int64_t b = b0 + q; b < b1; b += S) {
         const TV* A = vals + 49 * b + 7 * r;
         const TX* xb = x + 7 * (int64_t)col[b];
         TX s0 = TX(A[0]) * xb[0] + TX(A[1]) * xb[1];
@@ -48,9 +52,9 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __re
         acc += (s0 + s1) + (s2 + TX(A[6]) * xb[6]);
       }
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (lane < 28 && q == 0) y[7 * row + r] = (double)acc;
+#pragma unroll
+    for (int o = 1; o < S; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (r < 7 && q == 0 && row < n) y[7 * row + r] = (double)acc;
   }
 }
 
@@ -395,8 +399,11 @@ __global__ void __launch_bounds__(256) k_ras_apply(RasDev R, const TF* __restric
 
 template <class TV, class TX>
 void launch_bsr_spmv(int64_t n, const int64_t* row_ptr, const int32_t* col, const TV* vals, const TX* x,
-                     double* y, const int* guard, cudaStream_t s) {
-  k_bsr_spmv<TV, TX><<<grid_for(32 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y, guard);
+                     double* y, int threads_per_row, const int* guard, cudaStream_t s) {
+  if (threads_per_row == 16)
+    k_bsr_spmv<TV, TX, 2><<<grid_for(16 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y, guard);
+  else
+    k_bsr_spmv<TV, TX, 4><<<grid_for(32 * n, 256), 256, 0, s>>>(n, row_ptr, col, vals, x, y, guard);
 }
 
 void launch_to_float(int64_t n, const double* x, float* y, const int* guard, cudaStream_t s) {
@@ -461,9 +468,9 @@ void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* wor
 }
 
 template void launch_bsr_spmv<double, double>(int64_t, const int64_t*, const int32_t*, const double*,
-                                              const double*, double*, const int*, cudaStream_t);
+                                              const double*, double*, int, const int*, cudaStream_t);
 template void launch_bsr_spmv<float, float>(int64_t, const int64_t*, const int32_t*, const float*, const float*,
-                                            double*, const int*, cudaStream_t);
+                                            double*, int, const int*, cudaStream_t);
 template void launch_ras_extract<double, double>(const RasDev&, const double*, double*, cudaStream_t);
 template void launch_ras_extract<float, float>(const RasDev&, const float*, float*, cudaStream_t);
 template void launch_ras_factor<double>(const RasDev&, double*, int32_t*, cudaStream_t);
