@@ -125,6 +125,9 @@ typedef struct {
                              (global node order), 1 RCM, 2 RCM with lumen nodes
                              before interface and wall nodes */
   int32_t verbose;        /* print per-iteration norms to stderr */
+  int32_t fault_test;     /* tests only: 1 = the preconditioner apply's copy engine
+                             issues nothing, so the apply's bounded wait runs out and
+                             the call returns FSI_ERR_TIMEOUT; 0 otherwise */
 } fsi_options;
 
 typedef struct {

@@ -398,10 +398,16 @@ fsi_status gmres(fsi_ctx* c, fsi_solve_stats* st) {
     c->end_phase(h, PH_KRYLOV);
     CK(cudaMemcpyAsync(&c->hbuf[3], c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->s));
     CK(cudaMemcpyAsync(&c->hbuf[4], c->cyc + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(&c->hbuf[5], c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
     beta = c->hbuf[3];
-    int k = 0;
+    int k = 0, werr = 0;
     std::memcpy(&k, &c->hbuf[4], sizeof(int));
+    std::memcpy(&werr, &c->hbuf[5], sizeof(int32_t));
+    if (werr) {
+      CK(cudaMemsetAsync(c->errflag + 1, 0, sizeof(int32_t), c->s));
+      throw StatusError{FSI_ERR_TIMEOUT, "a bounded wait in the preconditioner apply gave up"};
+    }
     it += k;
     c->phase_n[PH_PCAPPLY] += k;
     c->phase_n[PH_SPMV] += k + 1;
@@ -409,13 +415,6 @@ fsi_status gmres(fsi_ctx* c, fsi_solve_stats* st) {
     if (c->opt.verbose) std::fprintf(stderr, "    gmres cycle: %d its, |r| = %.3e (target %.3e)\n", k, beta, target);
     conv = beta <= target;
     if (k == 0) break;  // no progress possible (breakdown at the first step)
-  }
-  if (c->use_stream) {
-    int32_t e = 0;
-    CK(cudaMemcpyAsync(&c->hbuf[2], c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaStreamSynchronize(c->s));
-    std::memcpy(&e, &c->hbuf[2], sizeof(int32_t));
-    if (e) throw StatusError{FSI_ERR_TIMEOUT, "a bounded wait in the preconditioner apply gave up"};
   }
   if (st) {
     st->iterations = it;
@@ -442,6 +441,7 @@ void fill_defaults(fsi_options* o) {
   o->threads_per_row = 32;
   o->ordering = 1;
   o->verbose = 0;
+  o->fault_test = 0;
 }
 
 }  // namespace
@@ -482,6 +482,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       o.threads_per_row = (q.threads_per_row == 16) ? 16 : 32;
       if (q.ordering >= 0 && q.ordering <= 2) o.ordering = q.ordering;
       o.verbose = q.verbose;
+      o.fault_test = q.fault_test;
     }
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
     if (o.ilu_level < 0 || o.ilu_level > 3) throw StatusError{FSI_ERR_ARG, "ilu_level must be 0..3"};
@@ -740,6 +741,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));
       const int64_t SB = std::max<int64_t>(maxblk, sbdef);
       rs.nst = nst;
+      rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       // row groups per stage
@@ -905,7 +907,15 @@ fsi_status fsi_pc_apply(fsi_ctx* c, const double* r, double* z) {
     if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
     if (c->pc_stale) pc_setup(c);
     pc_apply(c, r, z);
+    int32_t werr = 0;
+    CK(cudaMemcpyAsync(&c->hbuf[5], c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
+    std::memcpy(&werr, &c->hbuf[5], sizeof(int32_t));
+    if (werr) {
+      CK(cudaMemsetAsync(c->errflag + 1, 0, sizeof(int32_t), c->s));
+      CK(cudaStreamSynchronize(c->s));
+      throw StatusError{FSI_ERR_TIMEOUT, "a bounded wait in the preconditioner apply gave up"};
+    }
     return FSI_OK;
   });
 }

@@ -117,6 +117,7 @@ struct RasStreamDev {
   const int64_t* gU_nblk;
   int32_t max_groups;     // most L + U groups of one subdomain
   int32_t nst;            // ring stages in flight (2..8)
+  int32_t stall;          // tests only: the producer issues nothing (bounded waits run out)
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     if (lane == 0) {
       bool ok = true;
       int it = 0;
-      for (; it < ngroups; ++it) {
+      for (; it < ngroups && !R.stall; ++it) {
         const int st = it % NST;
         if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
         if (!ok) break;

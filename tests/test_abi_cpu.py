@@ -39,3 +39,50 @@ def test_default_options_and_argument_errors():
     assert L.fsi_step(None, None) == 1
     assert L.fsi_destroy(None) == 0
     assert L.fsi_last_error(None) == b"no context"
+
+
+def _mesh_struct(X, T, D, G):
+    import numpy as np
+    from paper_1810_04289_gb300 import fsi
+    keep = [np.ascontiguousarray(a) for a in (X, T, D, G)]
+    m = fsi.FsiMesh(X.shape[0], T.shape[0], keep[0].ctypes.data, keep[1].ctypes.data, keep[2].ctypes.data,
+                    keep[3].ctypes.data, None)
+    return m, keep
+
+
+def _create(m, opts):
+    import ctypes
+    from paper_1810_04289_gb300 import fsi
+    mat = fsi.FsiMaterial(1.05, 0.035, 1.2, 3e6, 0.45, 0.0)
+    bc = fsi.FsiBc()
+    bc.normal[:] = [0.0, 0.0, 1.0]
+    bc.radius = 1.0
+    ctx = ctypes.c_void_p()
+    st = fsi.lib().fsi_create(ctypes.byref(m), ctypes.byref(mat), ctypes.byref(bc), 1, ctypes.byref(opts), None,
+                              ctypes.byref(ctx))
+    return st, ctx
+
+
+def test_create_rejects_bad_meshes_and_options_on_the_host():
+    # validation runs before any device call, so these need no GPU
+    import numpy as np
+    import vesselmesh as vm
+    from paper_1810_04289_gb300 import fsi
+    box = vm.box_mesh(1, 1.0, domain=0)
+    X = box.X.astype(np.float64)
+    T = box.tets.astype(np.int32)
+    D = box.tet_domain.astype(np.uint8)
+    G = box.node_tag.astype(np.uint32)
+    bad = T.copy()
+    bad[0, 0] = 99                                  # vertex out of range
+    m, keep = _mesh_struct(X, bad, D, G)
+    st, ctx = _create(m, fsi.fsi_default_options())
+    assert st == 2 and not ctx.value
+    flipped = T.copy()
+    flipped[0, [2, 3]] = flipped[0, [3, 2]]        # negatively oriented tet
+    m, keep = _mesh_struct(X, flipped, D, G)
+    st, ctx = _create(m, fsi.fsi_default_options())
+    assert st == 2 and not ctx.value
+    m, keep = _mesh_struct(X, T, D, G)
+    st, ctx = _create(m, fsi.fsi_default_options(precision=5))
+    assert st == 1 and not ctx.value
