@@ -31,6 +31,9 @@ WORKLOADS = {
     "tube-96x32x15": dict(name="tube-96x32x15", kind="tube"),
     "tube-12x8x4": dict(name="tube-12x8x4", kind="tube"),
     "tube-160x48x22": dict(name="tube-160x48x22", kind="tube"),
+    "tree-3gen": dict(name="tree-3gen", kind="tree"),
+    "tree-3gen-h08": dict(name="tree-3gen", kind="tree", over=dict(h=0.08)),
+    "tree-7gen": dict(name="tree-7gen", kind="tree"),
 }
 MATERIAL = dict(rho_f=1.05, mu_f=0.035, rho_s=1.2, E_s=3.0e6, nu_s=0.45, eta_s=0.0)
 S_F64 = 8
@@ -58,7 +61,37 @@ def parse():
 
 def make_mesh(name):
     import vesselmesh as vm
-    return vm.tube_config(name)
+    w = WORKLOADS[name]
+    if w["kind"] == "tube":
+        return vm.tube_config(w["name"])
+    return vm.tree_config(w["name"], **w.get("over", {}))
+
+
+def initial_state(m, opt_base):
+    """Tubes: the Poiseuille field (no solve). Trees: one steady rigid-wall
+    Stokes solve at t = 0 (rho_f = 0, huge time step, wall clamped) from rest,
+    d = 0."""
+    import vesselmesh as vm
+    if m.info.get("kind") == "tube":
+        return vm.poiseuille_state(m)
+    from paper_1810_04289_gb300 import fsi
+    opt = fsi.FsiOptions()
+    for f, _ in fsi.FsiOptions._fields_:
+        setattr(opt, f, getattr(opt_base, f))
+    opt.dt = 1e8
+    opt.newton_rtol = 1e-8
+    opt.newton_maxit = 30
+    opt.gmres_rtol = 1e-6
+    opt.precision = 0
+    stokes = dict(MATERIAL, rho_f=0.0)
+    S = fsi.Solver(m, stokes, opt, rigid_wall=True)
+    y = np.zeros((m.n_nodes, 7))
+    S.set_state(y, t=-1e8)
+    S.step()
+    y, _ = S.state()
+    S.close()
+    y[:, 4:7] = 0.0
+    return y
 
 
 # ---------------------------------------------------------------------------
@@ -137,7 +170,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     m = make_mesh(args.workload)
-    y0 = vm.poiseuille_state(m)
+    y0 = initial_state(m, fsi.fsi_default_options(precision=1, n_subdomains=args.subdomains))
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):

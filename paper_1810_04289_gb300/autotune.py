@@ -4,7 +4,8 @@ For a mesh and a representative state it times, on the GPU and through the C
 ABI, one Newton linear system per candidate: preconditioner setup (extraction,
 ILU factorisation, packing) plus the GMRES solve to the candidate's tolerance.
 Candidates vary the Schwarz subdomain count, the overlap, the ILU fill level and
-the SpMV threads per block row; the fastest time to solution wins. The solver
+the SpMV threads per block row (default grid: see default_grid); the fastest
+converged time to solution wins. The solver
 arithmetic itself is unchanged by any choice (only the preconditioner and the
 launch mapping change), so the tuned options solve the same equations.
 """
@@ -13,7 +14,12 @@ import time
 
 from . import fsi
 
-DEFAULT_GRID = dict(n_subdomains=(128, 256, 512, 1024), overlap=(1,), ilu_level=(1,), threads_per_row=(32, 16))
+def default_grid(n_nodes):
+    """Subdomain counts (powers of two) giving 80..1000 nodes per subdomain, ILU(1)
+    and ILU(2) (the paper's defaults for its small and large meshes, Sec. 4.3,
+    4.7), overlap 1, one warp per SpMV block row."""
+    nps = [2 ** k for k in range(4, 16) if 80 <= n_nodes / 2 ** k <= 1000] or [max(1, n_nodes // 400)]
+    return dict(n_subdomains=tuple(nps), overlap=(1,), ilu_level=(1, 2), threads_per_row=(32,))
 
 
 def _time_linear_system(S, y, torch):
@@ -38,7 +44,7 @@ def autotune(mesh, material, y0, base=None, grid=None, t0=0.0, verbose=False):
     fsi_default_options()). grid: dict of option name -> tuple of values.
     """
     import torch
-    grid = dict(DEFAULT_GRID if grid is None else grid)
+    grid = dict(default_grid(mesh.n_nodes) if grid is None else grid)
     base = base if base is not None else fsi.fsi_default_options()
     names = list(grid)
     results = []

@@ -58,13 +58,11 @@ void build_gather(const BsrPattern& P, const std::vector<int32_t>& tets, std::ve
   const int64_t nnzb = (int64_t)P.col.size();
   std::vector<int64_t> blk(16 * T);
   bptr.assign(nnzb + 1, 0);
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < T; ++t)
     for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) {
-        int64_t k = find_block(P, tets[4 * t + a], tets[4 * t + b]);
-        blk[16 * t + 4 * a + b] = k;
-        bptr[k + 1]++;
-      }
+      for (int b = 0; b < 4; ++b) blk[16 * t + 4 * a + b] = find_block(P, tets[4 * t + a], tets[4 * t + b]);
+  for (int64_t q = 0; q < 16 * T; ++q) bptr[blk[q] + 1]++;
   for (int64_t k = 0; k < nnzb; ++k) bptr[k + 1] += bptr[k];
   bsrc.assign(16 * T, 0);
   std::vector<int64_t> f(bptr.begin(), bptr.end() - 1);
@@ -132,16 +130,26 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
   std::vector<std::vector<int32_t>> own(np);
   for (int64_t i = 0; i < n; ++i) own[owner[i]].push_back((int32_t)i);
 
+  // 2-5 per subdomain, independent: each subdomain builds its own plan (local
+  // positions) on one host thread, then the plans are concatenated in order
+  auto init_plan = [](RasPlan& L) {
+    L.sd_row.assign(1, 0);
+    L.row_ptr.assign(1, 0);
+    L.lent_ptr.assign(1, 0);
+    L.upd_ptr.assign(1, 0);
+    L.sd_lvlL.assign(1, 0);
+    L.sd_lvlU.assign(1, 0);
+    L.lvlL_ptr.assign(1, 0);
+    L.lvlU_ptr.assign(1, 0);
+  };
+  std::vector<RasPlan> subs(np);
+#pragma omp parallel
+  {
   std::vector<int32_t> loc(n, -1), mark(n, -1);
-  R.sd_row.assign(1, 0);
-  R.row_ptr.assign(1, 0);
-  R.lent_ptr.assign(1, 0);
-  R.upd_ptr.assign(1, 0);
-  R.sd_lvlL.assign(1, 0);
-  R.sd_lvlU.assign(1, 0);
-  R.lvlL_ptr.assign(1, 0);
-  R.lvlU_ptr.assign(1, 0);
+#pragma omp for schedule(dynamic, 1)
   for (int32_t s = 0; s < np; ++s) {
+    RasPlan& R = subs[s];
+    init_plan(R);
     // 2. overlap: delta layers of graph neighbours (Sec. 3, Omega_i^delta)
     std::vector<int32_t> nodes = own[s];
     for (int32_t v : nodes) mark[v] = s;
@@ -336,6 +344,40 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
     R.sd_row.push_back(r0 + m);
     for (int64_t q = 0; q < m; ++q) loc[gn[q]] = -1;
   }
+  }  // omp parallel
+
+  // concatenate: rows, blocks, L entries, updates and levels get the offsets of
+  // the subdomains before them
+  init_plan(R);
+  for (int32_t s = 0; s < np; ++s) {
+    RasPlan& L = subs[s];
+    const int64_t RO = (int64_t)R.gnode.size(), BO = (int64_t)R.col.size();
+    const int64_t LO = (int64_t)R.lent_pos.size(), UO = (int64_t)R.upd_tgt.size();
+    R.gnode.insert(R.gnode.end(), L.gnode.begin(), L.gnode.end());
+    R.owned.insert(R.owned.end(), L.owned.begin(), L.owned.end());
+    for (size_t i = 1; i < L.row_ptr.size(); ++i) R.row_ptr.push_back(L.row_ptr[i] + BO);
+    for (int32_t c : L.col) R.col.push_back((int32_t)(c + RO));
+    R.gblk.insert(R.gblk.end(), L.gblk.begin(), L.gblk.end());
+    for (int64_t d : L.diag) R.diag.push_back(d + BO);
+    for (size_t i = 1; i < L.lent_ptr.size(); ++i) R.lent_ptr.push_back(L.lent_ptr[i] + LO);
+    for (int64_t v : L.lent_pos) R.lent_pos.push_back(v + BO);
+    for (int64_t v : L.lent_kdiag) R.lent_kdiag.push_back(v + BO);
+    for (size_t i = 1; i < L.upd_ptr.size(); ++i) R.upd_ptr.push_back(L.upd_ptr[i] + UO);
+    for (int64_t v : L.upd_tgt) R.upd_tgt.push_back(v + BO);
+    for (int64_t v : L.upd_src) R.upd_src.push_back(v + BO);
+    const int64_t LLO = (int64_t)R.lvlL_rows.size(), ULO = (int64_t)R.lvlU_rows.size();
+    for (size_t i = 1; i < L.lvlL_ptr.size(); ++i) R.lvlL_ptr.push_back(L.lvlL_ptr[i] + LLO);
+    for (size_t i = 1; i < L.lvlU_ptr.size(); ++i) R.lvlU_ptr.push_back(L.lvlU_ptr[i] + ULO);
+    R.lvlL_rows.insert(R.lvlL_rows.end(), L.lvlL_rows.begin(), L.lvlL_rows.end());
+    R.lvlU_rows.insert(R.lvlU_rows.end(), L.lvlU_rows.begin(), L.lvlU_rows.end());
+    R.sd_lvlL.push_back((int64_t)R.lvlL_ptr.size() - 1);
+    R.sd_lvlU.push_back((int64_t)R.lvlU_ptr.size() - 1);
+    R.sd_row.push_back((int64_t)R.gnode.size());
+    R.max_levels = std::max(R.max_levels, L.max_levels);
+    R.max_rows = std::max(R.max_rows, L.max_rows);
+    L = RasPlan();  // release the per-subdomain memory early
+  }
+  R.np = np;
   return R;
 }
 

@@ -1,6 +1,6 @@
 """Kuhn-voxel meshes: a plain box (test meshes) and the bifurcating tree."""
 import numpy as np
-from .mesh import Mesh, FLUID, WALL, INLET, OUTLET, WALL_END, OUTER, orient_positive, tag_nodes
+from .mesh import Mesh, FLUID, WALL, INTERFACE, INLET, OUTLET, WALL_END, OUTER, orient_positive, tag_nodes
 
 _PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 
@@ -49,9 +49,183 @@ def box_mesh(n=3, h=1.0 / 3.0, domain=0, jitter=0.0, seed=0):
                 {"kind": "box", "n": n, "h": h})
 
 
-def tree_mesh(*a, **k):
-    raise NotImplementedError
+def _rotate(v, axis, ang):
+    """Rotate vector v about the unit axis by ang (Rodrigues)."""
+    axis = axis / np.linalg.norm(axis)
+    return (v * np.cos(ang) + np.cross(axis, v) * np.sin(ang) + axis * np.dot(axis, v) * (1 - np.cos(ang)))
 
 
-def tree_config(*a, **k):
-    raise NotImplementedError
+def tree_branches(generations, r0, ratio, ratio_noise=0.0, angle=(35.0, 60.0), length_factor=8.0,
+                  plane_jitter=20.0, seed=0):
+    """Seeded bifurcating tree of straight branches.
+
+    The root starts at the origin along +z with radius r0. Every branch ends in
+    a Y-bifurcation into two daughters of radius r * ratio * (1 +- ratio_noise),
+    each leaving the parent axis at an angle drawn from U(angle), on opposite
+    sides, in a plane rotated 90 deg +- U(plane_jitter) about the parent axis
+    from the parent's own branching plane. Branch length = length_factor * r.
+    Returns a list of dicts: p0, p1, radius, parent, leaf.
+    """
+    rng = np.random.default_rng(seed)
+    br = [dict(p0=np.zeros(3), p1=np.array([0.0, 0.0, length_factor * r0]), radius=r0, parent=-1,
+               plane=np.array([1.0, 0.0, 0.0]), gen=0)]
+    frontier = [0]
+    for g in range(1, generations):
+        nxt = []
+        for b in frontier:
+            P = br[b]
+            axis = (P["p1"] - P["p0"]) / np.linalg.norm(P["p1"] - P["p0"])
+            plane = _rotate(P["plane"], axis, np.deg2rad(90.0 + rng.uniform(-plane_jitter, plane_jitter)))
+            plane -= axis * np.dot(plane, axis)
+            plane /= np.linalg.norm(plane)
+            for side in (-1.0, 1.0):
+                th = np.deg2rad(rng.uniform(*angle))
+                d = np.cos(th) * axis + side * np.sin(th) * plane
+                r = P["radius"] * ratio * (1.0 + ratio_noise * rng.uniform(-1.0, 1.0))
+                br.append(dict(p0=P["p1"].copy(), p1=P["p1"] + length_factor * r * d, radius=r, parent=b,
+                               plane=plane, gen=g))
+                nxt.append(len(br) - 1)
+        frontier = nxt
+    children = {i: [] for i in range(len(br))}
+    for i, b in enumerate(br):
+        if b["parent"] >= 0:
+            children[b["parent"]].append(i)
+    for i, b in enumerate(br):
+        b["leaf"] = len(children[i]) == 0
+    return br
+
+
+def _branch_distance(pts, b, flat_start, flat_end):
+    """Distance from pts to the branch axis segment; inf where a flat cap cuts it off."""
+    d = b["p1"] - b["p0"]
+    L = np.linalg.norm(d)
+    d = d / L
+    rel = pts - b["p0"]
+    t = rel @ d
+    tc = np.clip(t, 0.0, L)
+    dist = np.linalg.norm(rel - tc[:, None] * d[None, :], axis=1)
+    if flat_start:
+        dist = np.where(t < 0.0, np.inf, dist)
+    if flat_end:
+        dist = np.where(t > L, np.inf, dist)
+    return dist
+
+
+def tree_mesh(generations=3, r0=1.2, ratio=0.79, ratio_noise=0.0, angle=(35.0, 60.0), length_factor=8.0,
+              wall=0.1, h=0.04, seed=0, peak=30.0, amp=0.5, freq=1.0 / 0.8, phase=0.0):
+    """Kuhn-voxel FSI mesh of a bifurcating tree (lumen + wall of fixed thickness).
+
+    Background grid of cubes of side h (z-planes through the inlet), 6 Kuhn
+    tets per cube; a tet is lumen if its centroid lies inside the union of the
+    branch capsules (flat cut at the root inlet and at every leaf outlet), wall
+    if it lies within `wall` outside that union, else dropped. The wet interface
+    comes from the face walk of Algorithm 1 (Sec. 4.8). Caps: fluid boundary
+    faces that are not interface faces lie on the inlet plane (INLET) or at a
+    leaf outlet (OUTLET); wall nodes within h/2 of a cap plane are WALL_END.
+    """
+    br = tree_branches(generations, r0, ratio, ratio_noise, angle, length_factor, seed=seed)
+    rmax_all = max(b["radius"] for b in br) + wall
+    pts_all = np.array([b["p0"] for b in br] + [b["p1"] for b in br])
+    lo = pts_all.min(axis=0) - rmax_all - 2 * h
+    hi = pts_all.max(axis=0) + rmax_all + 2 * h
+    lo[2] = 0.0                                   # the inlet plane z = 0 is a grid plane
+    n = np.ceil((hi - lo) / h).astype(np.int64)
+    # candidate cubes per branch (bounding box of the dilated capsule)
+    cubes = []
+    for i, b in enumerate(br):
+        R = b["radius"] + wall + h
+        bl = np.minimum(b["p0"], b["p1"]) - R
+        bh = np.maximum(b["p0"], b["p1"]) + R
+        i0 = np.maximum(np.floor((bl - lo) / h).astype(np.int64), 0)
+        i1 = np.minimum(np.ceil((bh - lo) / h).astype(np.int64), n)
+        gx, gy, gz = np.meshgrid(np.arange(i0[0], i1[0]), np.arange(i0[1], i1[1]), np.arange(i0[2], i1[2]),
+                                 indexing="ij")
+        c = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
+        ctr = lo + (c + 0.5) * h
+        dist = _branch_distance(ctr, b, b["parent"] < 0, b["leaf"])
+        keep = dist < b["radius"] + wall + 0.9 * h
+        cubes.append(c[keep])
+    cubes = np.unique(np.concatenate(cubes), axis=0)
+    # Kuhn tets of the candidate cubes, vertex ids on the global grid
+    def gid(ix, iy, iz):
+        return (iz * (n[1] + 1) + iy) * (n[0] + 1) + ix
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tv = []
+    for p in perms:
+        cc = np.zeros_like(cubes)
+        vs = [gid(cubes[:, 0], cubes[:, 1], cubes[:, 2])]
+        for ax in p:
+            cc[:, ax] += 1
+            vs.append(gid(cubes[:, 0] + cc[:, 0], cubes[:, 1] + cc[:, 1], cubes[:, 2] + cc[:, 2]))
+        tv.append(np.stack(vs, axis=1))
+    tv = np.concatenate(tv, axis=0)
+    # classify tets by centroid: min over branches of (distance - radius)
+    def coords(g):
+        ix = g % (n[0] + 1)
+        iy = (g // (n[0] + 1)) % (n[1] + 1)
+        iz = g // ((n[0] + 1) * (n[1] + 1))
+        return lo + np.stack([ix, iy, iz], axis=1) * h
+    ctr = sum(coords(tv[:, a]) for a in range(4)) / 4.0
+    gap = np.full(len(tv), np.inf)
+    for b in br:
+        gap = np.minimum(gap, _branch_distance(ctr, b, b["parent"] < 0, b["leaf"]) - b["radius"])
+    fluid = gap < 0.0
+    wallm = (~fluid) & (gap < wall)
+    keep = fluid | wallm
+    tv = tv[keep]
+    dom = np.where(fluid[keep], 0, 1).astype(np.uint8)
+    # compact node numbering in grid order (z-planes from the inlet)
+    ids, inv = np.unique(tv.ravel(), return_inverse=True)
+    tets = inv.reshape(-1, 4).astype(np.int64)
+    X = coords(ids)
+    tets = orient_positive(X, tets).astype(np.int32)
+    N = len(ids)
+    tag = tag_nodes(N, tets, dom)
+    # caps: fluid boundary faces that are not interface faces
+    from .mesh import TET_FACES
+    faces = tets.astype(np.int64)[:, TET_FACES].reshape(-1, 3)
+    owner = np.repeat(np.arange(len(tets)), 4)
+    key = np.sort(faces, axis=1)
+    _, finv, fcnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    bnd = fcnt[finv.ravel()] == 1
+    fl = (tag & FLUID) != 0
+    wl = (tag & WALL) != 0
+    fb = faces[bnd & (dom[owner] == 0)]
+    cap_nodes = np.unique(fb)
+    inlet = cap_nodes[np.abs(X[cap_nodes, 2]) < 1e-9]
+    tag[inlet] |= INLET
+    tag[np.setdiff1d(cap_nodes, inlet)] |= OUTLET
+    # wall ends: wall nodes within h/2 of the inlet plane or of a leaf's end plane
+    wend = wl & (np.abs(X[:, 2]) < 0.5 * h)
+    for b in br:
+        if b["leaf"]:
+            d = (b["p1"] - b["p0"]) / np.linalg.norm(b["p1"] - b["p0"])
+            t = (X - b["p1"]) @ d
+            near = np.linalg.norm((X - b["p1"]) - t[:, None] * d[None, :], axis=1) < b["radius"] + wall + h
+            wend |= wl & near & (np.abs(t) < 0.5 * h + 1e-12)
+    tag[wend] |= WALL_END
+    wb = faces[bnd & (dom[owner] == 1)]
+    outer = np.zeros(N, dtype=bool)
+    outer[np.unique(wb)] = True
+    tag[outer & wl & ~((tag & INTERFACE) != 0)] |= OUTER
+    inl = {"center": np.zeros(3), "normal": np.array([0.0, 0.0, 1.0]), "radius": float(r0), "peak": float(peak),
+           "amp": float(amp), "freq": float(freq), "phase": float(phase)}
+    info = {"kind": "tree", "generations": generations, "branches": len(br), "r0": r0, "ratio": ratio,
+            "ratio_noise": ratio_noise, "h": h, "wall": wall, "seed": seed, "length": float(hi[2] - lo[2]),
+            "leaves": int(sum(b["leaf"] for b in br))}
+    return Mesh(X, tets, dom, tag, np.zeros(N, dtype=np.int32), [inl], info)
+
+
+TREE_CONFIGS = {
+    # 3 generations of Y-bifurcations (7 branches), daughter ratio 0.79, root radius 1.2 cm
+    "tree-3gen": dict(generations=3, r0=1.2, ratio=0.79, h=0.04, seed=1810042890 + 2),
+    # 7 generations (127 branches), Murray ratio 2^(-1/3) with +-10% noise, root radius 1.4 cm
+    "tree-7gen": dict(generations=7, r0=1.4, ratio=2.0 ** (-1.0 / 3.0), ratio_noise=0.1, h=0.045,
+                      seed=1810042890 + 4),
+}
+
+
+def tree_config(name, **over):
+    kw = dict(TREE_CONFIGS[name])
+    kw.update(over)
+    return tree_mesh(**kw)
