@@ -242,19 +242,42 @@ __global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict
 }
 
 // Batched block ILU, whole CTA on one row: one CTA per subdomain walks its rows
-// in increasing order (a topological order of the elimination). The row, the
-// inverted pivots of its L blocks and all source blocks of its updates belong
-// to finished rows and are fetched into shared memory in one round trip; then
-// for each L block (i,k): threads 0..48 form A_ik D_k^{-1} into a separate
-// buffer (and the row), and all threads apply the block's updates
-// A_ij -= A_ik A_kj (task = update x column) - two barriers per L block.
+// in increasing order (a topological order of the elimination). At the start
+// of a row the row itself and the inverted pivots D_k of its L blocks (finished
+// rows) are loaded into shared memory; the source blocks A_kj of the updates of
+// each L block arrive by cp.async into a double buffer, one L block ahead, so
+// their memory latency hides behind the previous L block's arithmetic. For each
+// L block (i,k): threads 0..48 form A_ik D_k^{-1} (into a separate buffer and
+// the row), then all threads apply its updates A_ij -= A_ik A_kj (task =
+// update x column) - two barriers per L block.
+template <class TF>
+__device__ __forceinline__ void cp_async_elem(TF* dst, const TF* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(sizeof(TF))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <class TF>
+__device__ __forceinline__ void fetch_sources(const RasDev& R, const TF* fac, int64_t e, TF* buf, int tid, int nt) {
+  const int64_t ub = R.upd_ptr[e];
+  const int ne = (int)(R.upd_ptr[e + 1] - ub);
+  for (int idx = tid; idx < 49 * ne; idx += nt) {
+    const int u = idx / 49;
+    cp_async_elem<TF>(buf + idx, fac + 49 * R.upd_src[ub + u] + (idx - 49 * u));
+  }
+}
+
 template <class TF>
 __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict__ fac, int32_t* err) {
   extern __shared__ __align__(16) unsigned char fsm[];
+  const size_t me = (size_t)R.max_entry_upd * 49;
   TF* sRow = reinterpret_cast<TF*>(fsm);
   TF* sD = sRow + (size_t)R.max_row_blocks * 49;
-  TF* sSrc = sD + (size_t)R.max_row_lent * 49;
-  TF* sScl = sSrc + (size_t)R.max_row_upd * 49;
+  TF* sSrc0 = sD + (size_t)R.max_row_lent * 49;
+  TF* sSrc1 = sSrc0 + me;
+  TF* sScl = sSrc1 + me;
   TF* sAug = sScl + 49;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int s = blockIdx.x;
@@ -262,19 +285,20 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
     const int64_t rp = R.row_ptr[q];
     const int nblk = (int)(R.row_ptr[q + 1] - rp);
     const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
-    const int64_t u0 = R.upd_ptr[e0], u1 = R.upd_ptr[e1];
-    const int nl = (int)(e1 - e0), nu = (int)(u1 - u0);
+    const int nl = (int)(e1 - e0);
+    if (e0 < e1) fetch_sources<TF>(R, fac, e0, sSrc0, tid, nt);
+    cp_async_commit();
     for (int idx = tid; idx < 49 * nblk; idx += nt) sRow[idx] = fac[49 * rp + idx];
     for (int idx = tid; idx < 49 * nl; idx += nt) {
       const int e = idx / 49;
       sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
     }
-    for (int idx = tid; idx < 49 * nu; idx += nt) {
-      const int u = idx / 49;
-      sSrc[idx] = fac[49 * R.upd_src[u0 + u] + (idx - 49 * u)];
-    }
     __syncthreads();
     for (int64_t e = e0; e < e1; ++e) {
+      TF* cur = ((e - e0) & 1) ? sSrc1 : sSrc0;
+      TF* nxt = ((e - e0) & 1) ? sSrc0 : sSrc1;
+      if (e + 1 < e1) fetch_sources<TF>(R, fac, e + 1, nxt, tid, nt);
+      cp_async_commit();
       TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
       if (tid < 49) {
         const TF* Dk = sD + 49 * (e - e0);
@@ -284,6 +308,7 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
         for (int mm = 0; mm < 7; ++mm) v += Aik[7 * r + mm] * Dk[7 * mm + c];
         sScl[tid] = v;
       }
+      cp_async_wait1();  // this thread's copies of L block e have landed
       __syncthreads();
       if (tid < 49) Aik[tid] = sScl[tid];
       const int64_t ub = R.upd_ptr[e];
@@ -291,7 +316,7 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
       for (int t = tid; t < ntask; t += nt) {
         const int u = t / 7, cc = t - 7 * u;
         TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
-        const TF* Akj = sSrc + 49 * (ub + u - u0) + cc;
+        const TF* Akj = cur + 49 * u + cc;
         TF col[7];
 #pragma unroll
         for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
@@ -435,7 +460,7 @@ int ras_factor_warps(const RasDev& r, bool* all_out) {
 
 template <class TF>
 size_t ras_factor_cta_smem(const RasDev& r) {
-  return ((size_t)(r.max_row_blocks + r.max_row_lent + r.max_row_upd + 1) * 49 + 98) * sizeof(TF);
+  return ((size_t)(r.max_row_blocks + r.max_row_lent + 2 * r.max_entry_upd + 1) * 49 + 98) * sizeof(TF);
 }
 
 template <class TF>
