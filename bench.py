@@ -34,6 +34,7 @@ WORKLOADS = {
     "tree-3gen": dict(name="tree-3gen", kind="tree"),
     "tree-3gen-h08": dict(name="tree-3gen", kind="tree", over=dict(h=0.08)),
     "tree-7gen": dict(name="tree-7gen", kind="tree"),
+    "batch-64-tubes": dict(name="batch-64-tubes", kind="batch"),
 }
 MATERIAL = dict(rho_f=1.05, mu_f=0.035, rho_s=1.2, E_s=3.0e6, nu_s=0.45, eta_s=0.0)
 S_F64 = 8
@@ -64,15 +65,18 @@ def make_mesh(name):
     w = WORKLOADS[name]
     if w["kind"] == "tube":
         return vm.tube_config(w["name"])
+    if w["kind"] == "batch":
+        return vm.batch_tubes(n_tubes=64)
     return vm.tree_config(w["name"], **w.get("over", {}))
 
 
 def initial_state(m, opt_base):
-    """Tubes: the Poiseuille field (no solve). Trees: one steady rigid-wall
+    """Tubes (one or a batch): the Poiseuille field (no solve). Trees: one steady rigid-wall
     Stokes solve at t = 0 (rho_f = 0, huge time step, wall clamped) from rest,
     d = 0."""
     import vesselmesh as vm
-    if m.info.get("kind") == "tube":
+    kinds = [q.get("kind") for q in m.info.get("problems", [m.info])]
+    if all(k == "tube" for k in kinds):
         return vm.poiseuille_state(m)
     from paper_1810_04289_gb300 import fsi
     opt = fsi.FsiOptions()

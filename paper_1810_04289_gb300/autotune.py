@@ -61,9 +61,14 @@ def autotune(mesh, material, y0, base=None, grid=None, t0=0.0, verbose=False):
             results.append(dict(zip(names, values), error=str(e)))
             continue
         S.set_state(y0, t=t0)
-        # first solve builds the graph and warms the caches; the second is timed
-        _time_linear_system(S, y0, torch)
-        secs, its, conv = _time_linear_system(S, y0, torch)
+        try:
+            # first solve builds the graph and warms the caches; the second is timed
+            _time_linear_system(S, y0, torch)
+            secs, its, conv = _time_linear_system(S, y0, torch)
+        except fsi.FsiError as e:          # e.g. a singular pivot block of this ILU
+            results.append(dict(zip(names, values), error=str(e)))
+            S.close()
+            continue
         S.close()
         rec = dict(zip(names, values), seconds=secs, iterations=its, converged=bool(conv))
         results.append(rec)
@@ -72,5 +77,5 @@ def autotune(mesh, material, y0, base=None, grid=None, t0=0.0, verbose=False):
         if conv and (best is None or secs < best[0]):
             best = (secs, opt)
     if best is None:
-        raise RuntimeError("no candidate converged")
+        raise RuntimeError(f"no candidate converged: {results}")
     return best[1], results

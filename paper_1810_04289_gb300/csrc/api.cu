@@ -77,14 +77,23 @@ struct fsi_ctx {
   double t = 0.0;
   // Newton
   double *yk = nullptr, *ytr = nullptr, *F = nullptr, *Ft = nullptr, *dy = nullptr, *rhs = nullptr;
-  // GMRES
+  // GMRES, batched over the P problems (per-problem arrays are [P][...])
   int32_t m = 30;
-  double *V = nullptr, *Z = nullptr, *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *ylsq = nullptr;
-  double *hA = nullptr, *hB = nullptr, *partial = nullptr, *scal = nullptr, *r = nullptr;
-  double* gtarget = nullptr;     // device copy of the GMRES stopping threshold
-  int* cyc = nullptr;            // [0] cycle active, [1] columns done in the cycle
+  SegDev seg{};
+  double *V = nullptr, *Z = nullptr, *r = nullptr;
+  double *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *ylsq = nullptr, *hA = nullptr, *hB = nullptr;
+  double* partial = nullptr;     // [chunks][m+1] reduction partials
+  double* beta = nullptr;        // [P] norms (residual of the cycle, Newton norms)
+  double* gres = nullptr;        // [P] Givens residual estimates
+  double* gtarget = nullptr;     // [P] GMRES stopping thresholds
+  int* active = nullptr;         // [P] problem still iterating in the cycle
+  int* kcols = nullptr;          // [P] Krylov columns built in the cycle
+  int* anyact = nullptr;         // [1] some problem active (guard of the captured kernels)
+  int* pmask = nullptr;          // [P] problem already converged (Newton)
+  double* palpha = nullptr;      // [P] line-search step per problem
   float* zf = nullptr;           // FP32 copy of the SpMV input (mixed precision)
-  double* hbuf = nullptr;        // pinned host scalars
+  double* hbuf = nullptr;        // pinned host scratch (8 doubles + 4 P values)
+  std::vector<double> hvec;      // host copies of per-problem scalars
   // one GMRES cycle captured as a CUDA graph
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -188,12 +197,6 @@ fsi_status guarded(fsi_ctx* c, Fn&& fn) {
   }
 }
 
-double read_scalar(fsi_ctx* c, const double* dptr) {
-  CK(cudaMemcpyAsync(c->hbuf, dptr, sizeof(double), cudaMemcpyDeviceToHost, c->s));
-  CK(cudaStreamSynchronize(c->s));
-  return c->hbuf[0];
-}
-
 void check_launch() { CK(cudaGetLastError()); }
 
 // ---- F(y) for the step ending at t_n + dt (previous levels y_n, y_{n-1})
@@ -207,10 +210,19 @@ void residual(fsi_ctx* c, const double* y, double* F) {
   c->end_phase(h, PH_FUNC);
 }
 
-double norm(fsi_ctx* c, const double* x) {
+// per-problem 2-norms of x into c->hvec (host); returns the norm over all problems
+double norms(fsi_ctx* c, const double* x, std::vector<double>& out) {
   c->launches += 2;
-  launch_norm(c->n, x, c->partial, c->scal, nullptr, c->s);
-  return read_scalar(c, c->scal);
+  launch_seg_norm(c->seg, x, c->partial, c->beta, 1, nullptr, c->s);
+  out.resize(c->nprob);
+  CK(cudaMemcpyAsync(c->hbuf, c->beta, sizeof(double) * c->nprob, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  double tot = 0.0;
+  for (int p = 0; p < c->nprob; ++p) {
+    out[p] = c->hbuf[p];
+    tot += out[p] * out[p];
+  }
+  return std::sqrt(tot);
 }
 
 void jacobian(fsi_ctx* c, const double* y) {
@@ -309,32 +321,33 @@ void pc_apply(fsi_ctx* c, const double* rin, double* z) {
   c->end_phase(h, PH_PCAPPLY);
 }
 
-// One Arnoldi step j of the cycle (CGS2, normalisation, Givens), guarded.
+// One Arnoldi step j of the cycle for every problem (CGS2, normalisation,
+// Givens), guarded by "some problem still active".
 void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
   const int64_t n = c->n;
-  const int32_t ldh = c->m + 1;
+  const int32_t m = c->m, ldh = m + 1, P = c->nprob;
   double* w = c->V + (int64_t)(j + 1) * n;
-  double* Hj = c->H + (int64_t)j * ldh;
-  launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hA, guard, st);
-  launch_maxpy(n, j + 1, c->V, n, c->hA, w, guard, st);
-  launch_mdot(n, j + 1, c->V, n, w, c->partial, c->hB, guard, st);
-  launch_maxpy(n, j + 1, c->V, n, c->hB, w, guard, st);
-  launch_add_small(j + 1, c->hA, c->hB, Hj, guard, st);
-  launch_norm(n, w, c->partial, Hj + j + 1, guard, st);
-  launch_scale_inv(n, w, Hj + j + 1, w, guard, st);
-  launch_givens(c->H, ldh, j, c->cs, c->sn, c->g, c->scal + 1, c->gtarget, c->cyc, c->cyc + 1, st);
-  c->launches += 11;
+  launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
+  launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
+  launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
+  launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, guard, st);
+  launch_seg_add(P, j + 1, c->hA, c->hB, ldh, c->H, (int32_t)((int64_t)ldh * m), (int64_t)j * ldh, guard, st);
+  // H[p][j+1][j] = ||w_p||: norm into hA[p][0], copied into place by the Givens kernel's caller layout
+  launch_seg_norm(c->seg, w, c->partial, c->H + (int64_t)j * ldh + j + 1, ldh * m, guard, st);
+  launch_seg_scale_inv(c->seg, n, w, c->H + (int64_t)j * ldh + j + 1, ldh * m, w, guard, st);
+  launch_seg_givens(P, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active, c->kcols, c->anyact, st);
+  c->launches += 10;
 }
 
-// The kernels of one restart cycle, from V_0 = r / ||r|| to the true residual
-// of the updated iterate: c->rhs is b, c->dy is x, c->r the residual, c->scal[0]
-// its norm on entry and on exit.
+// The kernels of one restart cycle for every problem, from V_0 = r / ||r|| to
+// the true residual of the updated iterates: c->rhs is b, c->dy is x, c->r the
+// residual, c->beta[p] its norms on entry and on exit.
 void cycle_kernels(fsi_ctx* c, cudaStream_t st) {
   const int64_t n = c->n;
-  const int32_t m = c->m, ldh = m + 1;
-  const int* guard = c->cyc;
-  launch_scale_inv(n, c->r, c->scal, c->V, nullptr, st);
-  launch_cycle_init(c->g, ldh, c->scal, c->cyc, c->cyc + 1, st);
+  const int32_t m = c->m, ldh = m + 1, P = c->nprob;
+  const int* guard = c->anyact;
+  launch_seg_scale_inv(c->seg, n, c->r, c->beta, 1, c->V, nullptr, st);
+  launch_seg_cycle_init(P, c->g, ldh, c->beta, c->gtarget, c->active, c->kcols, c->anyact, st);
   c->launches += 2;
   for (int32_t j = 0; j < m; ++j) {
     double* vj = c->V + (int64_t)j * n;
@@ -344,12 +357,12 @@ void cycle_kernels(fsi_ctx* c, cudaStream_t st) {
     spmv_on(c, zj, c->mixed ? c->zf : nullptr, w, guard, st);
     arnoldi_step(c, j, guard, st);
   }
-  launch_lsq(c->H, ldh, 0, c->cyc + 1, c->g, c->ylsq, st);
-  launch_update_x(n, c->Z, n, c->ylsq, c->cyc + 1, c->dy, st);
+  launch_seg_lsq(P, c->H, ldh, m, c->kcols, c->g, c->ylsq, st);
+  launch_seg_update_x(c->seg, n, c->Z, n, c->ylsq, m, c->kcols, c->dy, st);
   c->launches += 2;
   spmv_on(c, c->dy, nullptr, c->r, nullptr, st);
   launch_axpby(n, 1.0, c->rhs, -1.0, c->r, c->r, st);
-  launch_norm(n, c->r, c->partial, c->scal, nullptr, st);
+  launch_seg_norm(c->seg, c->r, c->partial, c->beta, 1, nullptr, st);
   c->launches += 3;
 }
 
@@ -369,23 +382,33 @@ void build_graph(fsi_ctx* c) {
 
 // Right-preconditioned restarted flexible GMRES (FGMRES form: the preconditioned
 // directions Z are stored, so an FP32 preconditioner is allowed), classical
-// Gram-Schmidt applied twice, Givens rotations; each restart cycle runs as one
-// captured CUDA graph; the host checks the true residual once per cycle.
-// Solves J x = b with b = c->rhs, x = c->dy.
+// Gram-Schmidt applied twice, Givens rotations, run for every problem at once
+// with its own Krylov scalars and stopping test; each restart cycle is one
+// captured CUDA graph; the host reads the true residual norms once per cycle.
+// Solves J x = b with b = c->rhs, x = c->dy. Each problem stops when
+// ||b_p - J x_p|| <= gmres_rtol ||b_p||.
 fsi_status gmres(fsi_ctx* c, fsi_solve_stats* st) {
   if (!c->have_jac) throw StatusError{FSI_ERR_ARG, "no Jacobian assembled"};
   if (c->pc_stale) pc_setup(c);
   const int64_t n = c->n;
+  const int P = c->nprob;
   c->launches += 1;
   launch_fill(n, 0.0, c->dy, c->s);
   launch_copy(n, c->rhs, c->r, c->s);
-  double beta = norm(c, c->r);
-  const double rnorm0 = beta;
-  const double target = c->opt.gmres_rtol * beta;
-  CK(cudaMemcpyAsync(c->gtarget, &target, sizeof(double), cudaMemcpyHostToDevice, c->s));
+  std::vector<double> b0, bcur, target(P);
+  const double rnorm0 = norms(c, c->r, b0);
+  for (int p = 0; p < P; ++p) target[p] = c->opt.gmres_rtol * b0[p];
+  CK(cudaMemcpyAsync(c->gtarget, target.data(), sizeof(double) * P, cudaMemcpyHostToDevice, c->s));
+  auto all_conv = [&](const std::vector<double>& bb) {
+    for (int p = 0; p < P; ++p)
+      if (bb[p] > target[p]) return false;
+    return true;
+  };
+  bcur = b0;
   int32_t it = 0;
-  bool conv = beta <= target || beta == 0.0;
+  bool conv = all_conv(bcur);
   if (c->use_graph && !c->gexec) build_graph(c);
+  std::vector<int> kk(P);
   while (!conv && it < c->opt.gmres_maxit) {
     int h = c->begin_phase(PH_KRYLOV);
     if (c->use_graph) {
@@ -396,31 +419,42 @@ fsi_status gmres(fsi_ctx* c, fsi_solve_stats* st) {
     }
     check_launch();
     c->end_phase(h, PH_KRYLOV);
-    CK(cudaMemcpyAsync(&c->hbuf[3], c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(&c->hbuf[4], c->cyc + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(&c->hbuf[5], c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
+    double* hb = c->hbuf;
+    CK(cudaMemcpyAsync(hb, c->beta, sizeof(double) * P, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(hb + P, c->kcols, sizeof(int) * P, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(hb + 2 * P, c->errflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->s));
     CK(cudaStreamSynchronize(c->s));
-    beta = c->hbuf[3];
-    int k = 0, werr = 0;
-    std::memcpy(&k, &c->hbuf[4], sizeof(int));
-    std::memcpy(&werr, &c->hbuf[5], sizeof(int32_t));
+    int werr = 0;
+    std::memcpy(&werr, hb + 2 * P, sizeof(int32_t));
     if (werr) {
       CK(cudaMemsetAsync(c->errflag + 1, 0, sizeof(int32_t), c->s));
       throw StatusError{FSI_ERR_TIMEOUT, "a bounded wait in the preconditioner apply gave up"};
     }
-    it += k;
-    c->phase_n[PH_PCAPPLY] += k;
-    c->phase_n[PH_SPMV] += k + 1;
-    c->phase_n[PH_ORTH] += k;
-    if (c->opt.verbose) std::fprintf(stderr, "    gmres cycle: %d its, |r| = %.3e (target %.3e)\n", k, beta, target);
-    conv = beta <= target;
-    if (k == 0) break;  // no progress possible (breakdown at the first step)
+    std::memcpy(kk.data(), hb + P, sizeof(int) * P);
+    int kmax = 0;
+    for (int p = 0; p < P; ++p) {
+      bcur[p] = hb[p];
+      kmax = std::max(kmax, kk[p]);
+    }
+    it += kmax;
+    c->phase_n[PH_PCAPPLY] += kmax;
+    c->phase_n[PH_SPMV] += kmax + 1;
+    c->phase_n[PH_ORTH] += kmax;
+    conv = all_conv(bcur);
+    if (c->opt.verbose) {
+      double tot = 0;
+      for (double v : bcur) tot += v * v;
+      std::fprintf(stderr, "    gmres cycle: %d its, |r| = %.3e\n", kmax, std::sqrt(tot));
+    }
+    if (kmax == 0) break;  // no progress possible (breakdown at the first step)
   }
   if (st) {
+    double tot = 0;
+    for (double v : bcur) tot += v * v;
     st->iterations = it;
     st->converged = conv ? 1 : 0;
     st->rnorm0 = rnorm0;
-    st->rnorm = beta;
+    st->rnorm = std::sqrt(tot);
   }
   return conv ? FSI_OK : FSI_ERR_LINEAR_DIVERGED;
 }
@@ -442,6 +476,7 @@ void fill_defaults(fsi_options* o) {
   o->ordering = 1;
   o->verbose = 0;
   o->fault_test = 0;
+  o->factor_mode = 0;
 }
 
 }  // namespace
@@ -483,6 +518,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (q.ordering >= 0 && q.ordering <= 2) o.ordering = q.ordering;
       o.verbose = q.verbose;
       o.fault_test = q.fault_test;
+      if (q.factor_mode >= 0 && q.factor_mode <= 3) o.factor_mode = q.factor_mode;
     }
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
     if (o.ilu_level < 0 || o.ilu_level > 3) throw StatusError{FSI_ERR_ARG, "ilu_level must be 0..3"};
@@ -533,6 +569,8 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       const uint32_t tg = mesh->node_tag[i];
       const int32_t p = mesh->node_problem ? mesh->node_problem[i] : 0;
       if (p < 0 || p >= n_problems) throw StatusError{FSI_ERR_MESH, "node_problem out of range"};
+      if (i > 0 && p < prob[i - 1])
+        throw StatusError{FSI_ERR_MESH, "node_problem must be non-decreasing (problems stored one after another)"};
       prob[i] = p;
       const bool fl = tg & FSI_TAG_FLUID, wl = tg & FSI_TAG_WALL, itf = tg & FSI_TAG_INTERFACE;
       uint32_t f = 0;
@@ -629,20 +667,44 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     const int32_t m = cp->m;
     cp->V = cp->dalloc<double>((int64_t)(m + 1) * n);
     cp->Z = cp->dalloc<double>((int64_t)m * n);
-    cp->H = cp->dalloc<double>((int64_t)(m + 1) * m);
-    cp->g = cp->dalloc<double>(m + 1);
-    cp->cs = cp->dalloc<double>(m);
-    cp->sn = cp->dalloc<double>(m);
-    cp->ylsq = cp->dalloc<double>(m);
-    cp->hA = cp->dalloc<double>(m + 1);
-    cp->hB = cp->dalloc<double>(m + 1);
-    cp->partial = cp->dalloc<double>((int64_t)RED_BLOCKS * (m + 2));
-    cp->scal = cp->dalloc<double>(4);
+    const int64_t NP = n_problems;
+    cp->H = cp->dalloc<double>(NP * (m + 1) * m);
+    cp->g = cp->dalloc<double>(NP * (m + 1));
+    cp->cs = cp->dalloc<double>(NP * m);
+    cp->sn = cp->dalloc<double>(NP * m);
+    cp->ylsq = cp->dalloc<double>(NP * m);
+    cp->hA = cp->dalloc<double>(NP * (m + 1));
+    cp->hB = cp->dalloc<double>(NP * (m + 1));
+    // reduction chunks: each problem's dofs cut into chunks of at most CH dofs
+    {
+      const int64_t CH = std::max<int64_t>(1024, (7 * N + 1215) / 1216);
+      std::vector<int64_t> cb{0}, pc{0};
+      std::vector<int64_t> pstart(NP + 1, 0);
+      for (int64_t i = 0; i < N; ++i) pstart[prob[i] + 1]++;
+      for (int64_t q = 0; q < NP; ++q) pstart[q + 1] += pstart[q];
+      for (int64_t q = 0; q < NP; ++q) {
+        const int64_t a0 = 7 * pstart[q], a1 = 7 * pstart[q + 1];
+        for (int64_t x = a0; x < a1; x += CH) cb.push_back(std::min(a1, x + CH));
+        pc.push_back((int64_t)cb.size() - 1);
+      }
+      cp->seg.P = (int32_t)NP;
+      cp->seg.n_chunks = (int64_t)cb.size() - 1;
+      cp->seg.chunk_beg = cp->upload(cb);
+      cp->seg.prob_chunk = cp->upload(pc);
+      cp->seg.node_prob = cp->nprobid;
+      cp->partial = cp->dalloc<double>(cp->seg.n_chunks * (m + 1));
+    }
+    cp->beta = cp->dalloc<double>(n_problems);
+    cp->gres = cp->dalloc<double>(n_problems);
+    cp->active = cp->dalloc<int>(n_problems);
+    cp->kcols = cp->dalloc<int>(n_problems);
+    cp->anyact = cp->dalloc<int>(1);
+    cp->pmask = cp->dalloc<int>(n_problems);
+    cp->palpha = cp->dalloc<double>(n_problems);
     cp->r = cp->dalloc<double>(n);
-    cp->gtarget = cp->dalloc<double>(1);
-    cp->cyc = cp->dalloc<int>(2);
+    cp->gtarget = cp->dalloc<double>(n_problems);
     cp->zf = cp->dalloc<float>(n);
-    CK(cudaMallocHost(&cp->hbuf, 64));
+    CK(cudaMallocHost(&cp->hbuf, sizeof(double) * (3 * n_problems + 16)));
 
     // Schwarz plan
     RasPlan& R = cp->plan;
@@ -681,8 +743,21 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rd.max_row_lent = (int32_t)ml;
       rd.max_row_upd = (int32_t)mu;
       rd.max_entry_upd = (int32_t)me;
-      const int nw = cp->mixed ? ras_factor_warps<float>(rd, nullptr) : ras_factor_warps<double>(rd, nullptr);
-      if (nw < 1) throw StatusError{FSI_ERR_ARG, "ILU rows too long for the shared-memory factorisation"};
+      const int fm = cp->mixed ? ras_factor_mode<float>(rd, nullptr) : ras_factor_mode<double>(rd, nullptr);
+      if (fm >= 0 && o.factor_mode > 0) {
+        if (o.factor_mode - 1 < fm) throw StatusError{FSI_ERR_ARG, "factor_mode needs more shared memory than fits"};
+        rd.factor_mode = o.factor_mode - 1;
+      } else {
+        rd.factor_mode = fm;
+      }
+      if (fm < 0) {
+        char msg[192];
+        std::snprintf(msg, sizeof msg,
+                      "ILU rows too long for the shared-memory factorisation (%d blocks in the longest row; "
+                      "use a lower fill level or more subdomains)",
+                      rd.max_row_blocks);
+        throw StatusError{FSI_ERR_ARG, msg};
+      }
 
     }
     cp->ras = rd;
@@ -945,72 +1020,93 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, c->s));
     const int64_t n = c->n;
+    const int P = c->nprob;
     launch_copy(n, c->yn, c->yk, c->s);
     residual(c, c->yk, c->F);
     S.residual_evaluations++;
-    double nf = norm(c, c->F);
-    const double nf0 = nf;
-    S.fnorm0 = nf0;
-    if (!std::isfinite(nf)) throw StatusError{FSI_ERR_NONFINITE, "non-finite residual"};
+    // Newton per problem (Eq. 11-12): every problem has its own norm, stopping
+    // test and line-search step; converged problems keep their iterate
+    std::vector<double> nf, nf0, nft;
+    double tot = norms(c, c->F, nf);
+    nf0 = nf;
+    S.fnorm0 = tot;
+    if (!std::isfinite(tot)) throw StatusError{FSI_ERR_NONFINITE, "non-finite residual"};
     const double stall = 1e-8;
+    std::vector<int> conv(P, 0), pend(P, 0);
+    std::vector<double> alpha(P, 0.0);
+    auto test_conv = [&](int p) { return nf[p] <= c->opt.newton_rtol * nf0[p] || nf[p] <= c->opt.newton_atol; };
+    for (int p = 0; p < P; ++p) conv[p] = test_conv(p);
+    auto all_done = [&]() {
+      for (int p = 0; p < P; ++p)
+        if (!conv[p]) return false;
+      return true;
+    };
     int32_t it = 0;
-    bool conv = false;
-    while (true) {
-      if (nf <= c->opt.newton_rtol * nf0 || nf <= c->opt.newton_atol) {
-        conv = true;
-        break;
-      }
-      if (it >= c->opt.newton_maxit) break;
+    while (!all_done()) {
+      if (it >= c->opt.newton_maxit) throw StatusError{FSI_ERR_DIVERGED, "Newton reached its iteration limit"};
       if (it % c->opt.jac_lag == 0) {
         jacobian(c, c->yk);
         S.jacobian_evaluations++;
       }
+      CK(cudaMemcpyAsync(c->pmask, conv.data(), sizeof(int) * P, cudaMemcpyHostToDevice, c->s));
       c->launches += 1;
-      launch_axpby(n, -1.0, c->F, 0.0, c->F, c->rhs, c->s);
+      launch_seg_neg_masked(c->seg, n, c->F, c->pmask, c->rhs, c->s);   // rhs = -F on unconverged problems
       fsi_solve_stats ls{};
       fsi_status lst = gmres(c, &ls);
       if (lst != FSI_OK && lst != FSI_ERR_LINEAR_DIVERGED) return lst;
       S.linear_iterations += ls.iterations;
       if (c->opt.verbose)
-        std::fprintf(stderr, "  newton %d: |F| = %.6e, gmres %d its (%.2e -> %.2e)\n", it, nf, ls.iterations,
+        std::fprintf(stderr, "  newton %d: |F| = %.6e, gmres %d its (%.2e -> %.2e)\n", it, tot, ls.iterations,
                      ls.rnorm0, ls.rnorm);
-      // backtracking line search
-      double alpha = 1.0, nft = 0.0;
-      bool ok = false;
-      while (true) {
+      // backtracking line search, per problem
+      for (int p = 0; p < P; ++p) {
+        alpha[p] = conv[p] ? 0.0 : 1.0;
+        pend[p] = !conv[p];
+      }
+      bool any_pending = true;
+      while (any_pending) {
+        CK(cudaMemcpyAsync(c->palpha, alpha.data(), sizeof(double) * P, cudaMemcpyHostToDevice, c->s));
         c->launches += 1;
-        launch_axpby(n, 1.0, c->yk, alpha, c->dy, c->ytr, c->s);
+        launch_seg_axpy(c->seg, n, c->yk, c->palpha, c->dy, c->ytr, c->s);
         residual(c, c->ytr, c->Ft);
         S.residual_evaluations++;
-        nft = norm(c, c->Ft);
-        if (std::isfinite(nft) && nft <= (1.0 - 1e-4 * alpha) * nf) {
-          ok = true;
-          break;
+        norms(c, c->Ft, nft);
+        any_pending = false;
+        for (int p = 0; p < P; ++p) {
+          if (!pend[p]) continue;
+          if (std::isfinite(nft[p]) && nft[p] <= (1.0 - 1e-4 * alpha[p]) * nf[p]) {
+            pend[p] = 0;
+            continue;
+          }
+          alpha[p] *= 0.5;
+          if (alpha[p] < 1.0 / 1024.0) {
+            if (nf[p] <= stall * nf0[p]) {  // |F_p| sits at the rounding floor of its assembly
+              alpha[p] = 0.0;
+              conv[p] = 1;
+              pend[p] = 0;
+              continue;
+            }
+            throw StatusError{FSI_ERR_LINESEARCH, "backtracking line search found no sufficient decrease"};
+          }
+          any_pending = true;
         }
-        alpha *= 0.5;
-        if (alpha < 1.0 / 1024.0) break;
       }
-      if (!ok) {
-        if (nf <= stall * nf0) {
-          conv = true;  // |F| sits at the rounding floor of its assembly
-          break;
-        }
-        throw StatusError{FSI_ERR_LINESEARCH, "backtracking line search found no sufficient decrease"};
-      }
-      const bool stalled = nft > 0.5 * nf && nft <= stall * nf0;
       std::swap(c->yk, c->ytr);
       std::swap(c->F, c->Ft);
-      nf = nft;
-      ++it;
-      if (stalled) {
-        conv = true;
-        break;
+      for (int p = 0; p < P; ++p) {
+        if (conv[p]) continue;
+        const bool stalled = nft[p] > 0.5 * nf[p] && nft[p] <= stall * nf0[p];
+        nf[p] = nft[p];
+        conv[p] = test_conv(p) || stalled;
       }
+      tot = 0.0;
+      for (int p = 0; p < P; ++p) tot += nf[p] * nf[p];
+      tot = std::sqrt(tot);
+      ++it;
     }
     S.newton_iterations = it;
-    S.fnorm = nf;
-    S.converged = conv ? 1 : 0;
-    if (!conv) throw StatusError{FSI_ERR_DIVERGED, "Newton reached its iteration limit"};
+    S.fnorm = tot;
+    S.converged = 1;
     // shift time levels: y_{n-2} <- y_{n-1} <- y_n <- y
     double* old2 = c->ynm2;
     c->ynm2 = c->ynm1;

@@ -76,13 +76,18 @@ struct RasDev {
   int32_t max_row_lent;    // most L blocks in one row
   int32_t max_row_upd;     // most elimination updates in one row
   int32_t max_entry_upd;   // most updates of one L block
+  int32_t factor_mode;     // shared-memory mode of the factorisation CTA (0..2)
 };
 template <class TF, class TJ>
 void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s);
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
 template <class TF>
-int ras_factor_warps(const RasDev& r, bool* all_out);  // 0: rows too long for shared memory
+int ras_factor_mode(const RasDev& r, size_t* smem);  // -1: a row does not fit in shared memory
+// shared-memory limits of the factorisation CTA: the prefetching mode is used
+// up to FACTOR_SMEM_PREFERRED, the leaner ones up to the opt-in maximum
+constexpr size_t FACTOR_SMEM_PREFERRED = 200 * 1024;
+constexpr size_t FACTOR_SMEM_MAX = 227 * 1024;
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,
                       const int* guard, cudaStream_t s);
@@ -131,28 +136,42 @@ template <class TF>
 cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, float* z32, int32_t* err,
                                     const int* guard, cudaStream_t s);
 
-// ---- Krylov / BLAS-1 (krylov.cu); vectors of n doubles. guard: optional
-// device flag; guarded kernels do nothing while *guard == 0.
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs, fixed so that reductions are deterministic
-void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                 double* out, const int* guard, cudaStream_t s);
-void launch_maxpy(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h, double* w,
-                  const int* guard, cudaStream_t s);
-void launch_norm(int64_t n, const double* x, double* partial, double* out, const int* guard, cudaStream_t s);
-void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, const int* guard,
-                      cudaStream_t s);
+// ---- batched Krylov / BLAS-1 (krylov.cu): vectors of n doubles holding P
+// independent problems one after the other; reductions are segmented by
+// problem over a fixed chunk table (deterministic). guard: optional device
+// flag; guarded kernels do nothing while *guard == 0.
+struct SegDev {
+  int32_t P;                 // problems
+  int64_t n_chunks;
+  const int64_t* chunk_beg;  // [n_chunks+1] first dof of each chunk (chunks never straddle problems)
+  const int64_t* prob_chunk; // [P+1] chunks of each problem
+  const int32_t* node_prob;  // [N] problem of each node
+};
+void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
+                     double* out, int32_t ldo, const int* guard, cudaStream_t s);
+void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
+                     const int* guard, cudaStream_t s);
+void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,
+                      int32_t ldh, double* w, const int* guard, cudaStream_t s);
+void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const double* scal, int32_t lds,
+                          double* y, const int* guard, cudaStream_t s);
+void launch_seg_add(int32_t P, int32_t nv, const double* a, const double* b, int32_t lda, double* H, int32_t ldHp,
+                    int64_t colofs, const int* guard, cudaStream_t s);
+void launch_seg_cycle_init(int32_t P, double* g, int32_t ldg, const double* beta, const double* target, int* active,
+                           int* kcols, int* any, cudaStream_t s);
+void launch_seg_givens(int32_t P, double* H, int32_t ldh, int32_t m, int32_t j, double* cs, double* sn, double* g,
+                       double* res, const double* target, int* active, int* kcols, int* any, cudaStream_t s);
+void launch_seg_lsq(int32_t P, const double* H, int32_t ldh, int32_t m, const int* kcols, const double* g, double* y,
+                    cudaStream_t s);
+void launch_seg_update_x(const SegDev& sg, int64_t n, const double* Z, int64_t ldz, const double* y, int32_t m,
+                         const int* kcols, double* x, cudaStream_t s);
+void launch_seg_axpy(const SegDev& sg, int64_t n, const double* x, const double* alpha, const double* y, double* out,
+                     cudaStream_t s);
+void launch_seg_neg_masked(const SegDev& sg, int64_t n, const double* x, const int* mask, double* out,
+                           cudaStream_t s);
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out,
                   cudaStream_t s);
 void launch_copy(int64_t n, const double* x, double* y, cudaStream_t s);
 void launch_fill(int64_t n, double v, double* x, cudaStream_t s);
-void launch_add_small(int32_t nv, const double* a, const double* b, double* out, const int* guard,
-                      cudaStream_t s);
-void launch_cycle_init(double* g, int32_t ldh, const double* scal, int* active, int* kcols, cudaStream_t s);
-void launch_givens(double* H, int32_t ldh, int32_t j, double* cs, double* sn, double* g, double* res,
-                   const double* target, int* active, int* kcols, cudaStream_t s);
-void launch_lsq(const double* H, int32_t ldh, int32_t k, const int* kdev, const double* g, double* y,
-                cudaStream_t s);
-void launch_update_x(int64_t n, const double* Z, int64_t ldz, const double* y, const int* kdev, double* x,
-                     cudaStream_t s);
 
 }  // namespace fsi

@@ -1,12 +1,14 @@
-// FP64 vector kernels of the Krylov loop: multi-dot products for classical
-// Gram-Schmidt (twice), multi-axpy, norms, scaling, Givens rotations and the
-// Hessenberg least-squares solve. Reductions use a fixed grid of RED_BLOCKS
-// blocks and a second pass in fixed order, so results are bitwise
-// reproducible run to run.
+// FP64 vector kernels of the batched Krylov loop. The unknowns of P independent
+// problems are stored one after the other; every reduction is segmented by
+// problem: a fixed table of chunks (each inside one problem) is reduced by one
+// block per chunk, then each problem sums its chunks in fixed order, so results
+// are bitwise reproducible run to run and independent problems never mix.
+// Per-problem Arnoldi scalars: H (column-major (m+1) x m per problem), g, Givens
+// cs/sn, residual estimates, stop flags.
 //
 // Kernels that run inside a captured GMRES cycle take a guard pointer: while
-// *guard == 0 (the cycle has converged or broken down) they return at once, so
-// the remaining iterations of the captured cycle cost only their launches.
+// *guard == 0 (every problem has converged or broken down) they return at once,
+// so the rest of the captured cycle costs only its launches.
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -26,21 +28,23 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[blockIdx.x * ldp + k] = sum over this block's rows of V_k . w
-__global__ void __launch_bounds__(RB) k_mdot(int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
-                                             const double* __restrict__ w, double* __restrict__ partial,
-                                             int32_t ldp, const int* guard) {
+// partial[c * ldp + k] = sum over chunk c of V_k . w (V_k = w itself if V is null: squared norm)
+__global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const double* __restrict__ V, int64_t ldv,
+                                                 const double* __restrict__ w, double* __restrict__ partial,
+                                                 int32_t ldp, const int* guard) {
   if (off(guard)) return;
   __shared__ double red[MD][RB / 32];
+  const int c = blockIdx.x;
   const int k0 = blockIdx.y * MD;
+  const int64_t i0 = sg.chunk_beg[c], i1 = sg.chunk_beg[c + 1];
   double acc[MD];
 #pragma unroll
   for (int k = 0; k < MD; ++k) acc[k] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += RB) {
     const double wi = w[i];
 #pragma unroll
     for (int k = 0; k < MD; ++k)
-      if (k0 + k < nv) acc[k] += V[(int64_t)(k0 + k) * ldv + i] * wi;
+      if (k0 + k < nv) acc[k] += (V ? V[(int64_t)(k0 + k) * ldv + i] : wi) * wi;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -52,63 +56,171 @@ __global__ void __launch_bounds__(RB) k_mdot(int64_t n, int32_t nv, const double
   if (threadIdx.x < MD && k0 + threadIdx.x < nv) {
     double v = 0.0;
     for (int q = 0; q < RB / 32; ++q) v += red[threadIdx.x][q];
-    partial[(int64_t)blockIdx.x * ldp + k0 + threadIdx.x] = v;
+    partial[(int64_t)c * ldp + k0 + threadIdx.x] = v;
   }
 }
 
-__global__ void k_reduce_partials(int32_t nv, const double* __restrict__ partial, int32_t ldp, int32_t nb,
-                                  double* __restrict__ out, int take_sqrt, const int* guard) {
+// out[p * ldo + k] = sum over the chunks of problem p of partial[c * ldp + k]:
+// one block per problem, one warp per k, lanes over the chunks (fixed order)
+__global__ void k_seg_reduce(SegDev sg, int32_t nv, const double* __restrict__ partial, int32_t ldp,
+                             double* __restrict__ out, int32_t ldo, int take_sqrt, const int* guard) {
   if (off(guard)) return;
-  __shared__ double red[RB / 32];
-  for (int k = 0; k < nv; ++k) {
+  const int p = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t c0 = sg.prob_chunk[p], c1 = sg.prob_chunk[p + 1];
+  for (int k = warp; k < nv; k += nw) {
     double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[(int64_t)b * ldp + k];
+    for (int64_t c = c0 + lane; c < c1; c += 32) v += partial[c * ldp + k];
     v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-      out[k] = take_sqrt ? sqrt(s) : s;
-    }
-    __syncthreads();
+    if (lane == 0) out[(int64_t)p * ldo + k] = take_sqrt ? sqrt(v) : v;
   }
 }
 
-// w -= sum_k h[k] V_k
-__global__ void k_maxpy(int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
-                        const double* __restrict__ h, double* __restrict__ w, const int* guard) {
+// w_i -= sum_k h[p(i)][k] V_k[i]
+__global__ void k_seg_maxpy(SegDev sg, int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
+                            const double* __restrict__ h, int32_t ldh, double* __restrict__ w, const int* guard) {
   if (off(guard)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double* hp = h + (int64_t)sg.node_prob[i / 7] * ldh;
     double s = w[i];
-    for (int k = 0; k < nv; ++k) s -= h[k] * V[(int64_t)k * ldv + i];
+    for (int k = 0; k < nv; ++k) s -= hp[k] * V[(int64_t)k * ldv + i];
     w[i] = s;
   }
 }
 
-__global__ void k_norm_partial(int64_t n, const double* __restrict__ x, double* __restrict__ partial,
-                               const int* guard) {
+// y_i = x_i / scal[p(i) * lds] (0 where the scale is 0)
+__global__ void k_seg_scale_inv(SegDev sg, int64_t n, const double* __restrict__ x, const double* __restrict__ scal,
+                                int32_t lds, double* __restrict__ y, const int* guard) {
   if (off(guard)) return;
-  __shared__ double red[RB / 32];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) acc += x[i] * x[i];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < RB / 32; ++q) s += red[q];
-    partial[blockIdx.x] = s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = scal[(int64_t)sg.node_prob[i / 7] * lds];
+    y[i] = a != 0.0 ? x[i] / a : 0.0;
   }
 }
 
-__global__ void k_scale_inv(int64_t n, const double* __restrict__ x, const double* __restrict__ scal,
-                            double* __restrict__ y, const int* guard) {
+// H[p][:, j] = a[p] + b[p] (the two classical Gram-Schmidt passes), first j+1 entries
+__global__ void k_seg_add(int32_t P, int32_t nv, const double* __restrict__ a, const double* __restrict__ b,
+                          int32_t lda, double* __restrict__ H, int32_t ldHp, int64_t colofs, const int* guard) {
   if (off(guard)) return;
-  const double a = *scal;
-  const double inv = a != 0.0 ? 1.0 / a : 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)P * nv;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx / nv;
+    const int k = (int)(idx - p * nv);
+    H[p * ldHp + colofs + k] = a[p * lda + k] + b[p * lda + k];
+  }
+}
+
+// start of a cycle for every problem: g = beta e_1, active while beta > target
+__global__ void k_seg_cycle_init(int32_t P, double* __restrict__ g, int32_t ldg, const double* __restrict__ beta,
+                                 const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kcols,
+                                 int* __restrict__ any) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    for (int k = 0; k < ldg; ++k) g[(int64_t)p * ldg + k] = k == 0 ? beta[p] : 0.0;
+    const int a = beta[p] > target[p] ? 1 : 0;
+    active[p] = a;
+    kcols[p] = 0;
+    if (a) atomicOr(&s_any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *any = s_any;
+}
+
+// Givens update of column j of every active problem's Hessenberg: apply the
+// previous rotations, form the one that zeroes H[j+1][j], rotate g; |g[j+1]|
+// is that problem's GMRES residual. A problem stops at its target or when its
+// Krylov space is exhausted (H[j+1][j] = 0). *any = some problem still active.
+__global__ void k_seg_givens(int32_t P, double* __restrict__ H, int32_t ldh, int32_t m, int32_t j,
+                             double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                             double* __restrict__ res, const double* __restrict__ target, int* __restrict__ active,
+                             int* __restrict__ kcols, int* __restrict__ any) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    if (active[p]) {
+      double* h = H + (int64_t)p * ldh * m + (int64_t)j * ldh;
+      double* c_ = cs + (int64_t)p * m;
+      double* s_ = sn + (int64_t)p * m;
+      double* gp = g + (int64_t)p * ldh;
+      const double sub = h[j + 1];
+      for (int i = 0; i < j; ++i) {
+        const double a = h[i], b = h[i + 1];
+        h[i] = c_[i] * a + s_[i] * b;
+        h[i + 1] = -s_[i] * a + c_[i] * b;
+      }
+      const double a = h[j], b = h[j + 1];
+      const double r = hypot(a, b);
+      double c = 1.0, sv = 0.0;
+      if (r > 0.0) {
+        c = a / r;
+        sv = b / r;
+      }
+      c_[j] = c;
+      s_[j] = sv;
+      h[j] = r;
+      h[j + 1] = 0.0;
+      const double gj = gp[j];
+      gp[j] = c * gj;
+      gp[j + 1] = -sv * gj;
+      const double rn = fabs(gp[j + 1]);
+      res[p] = rn;
+      kcols[p] = j + 1;
+      if (!(rn > target[p]) || sub == 0.0) active[p] = 0;
+    }
+    if (active[p]) atomicOr(&s_any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *any = s_any;
+}
+
+// y[p] = R_p^{-1} g[p] for each problem's kcols[p] x kcols[p] rotated Hessenberg
+__global__ void k_seg_lsq(int32_t P, const double* __restrict__ H, int32_t ldh, int32_t m,
+                          const int* __restrict__ kcols, const double* __restrict__ g, double* __restrict__ y) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const int k = kcols[p];
+    const double* Hp = H + (int64_t)p * ldh * m;
+    const double* gp = g + (int64_t)p * ldh;
+    double* yp = y + (int64_t)p * m;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gp[i];
+      for (int jj = i + 1; jj < k; ++jj) s -= Hp[(int64_t)jj * ldh + i] * yp[jj];
+      const double d = Hp[(int64_t)i * ldh + i];
+      yp[i] = d != 0.0 ? s / d : 0.0;
+    }
+  }
+}
+
+// x_i += sum_{q < kcols[p(i)]} y[p(i)][q] Z_q[i]
+__global__ void k_seg_update_x(SegDev sg, int64_t n, const double* __restrict__ Z, int64_t ldz,
+                               const double* __restrict__ y, int32_t m, const int* __restrict__ kcols,
+                               double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = sg.node_prob[i / 7];
+    const int k = kcols[p];
+    const double* yp = y + (int64_t)p * m;
+    double s = x[i];
+    for (int q = 0; q < k; ++q) s += yp[q] * Z[(int64_t)q * ldz + i];
+    x[i] = s;
+  }
+}
+
+// out_i = x_i + alpha[p(i)] y_i
+__global__ void k_seg_axpy(SegDev sg, int64_t n, const double* __restrict__ x, const double* __restrict__ alpha,
+                           const double* __restrict__ y, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = alpha[sg.node_prob[i / 7]];
+    out[i] = a != 0.0 ? x[i] + a * y[i] : x[i];
+  }
+}
+
+// out_i = mask[p(i)] ? 0 : -x_i
+__global__ void k_seg_neg_masked(SegDev sg, int64_t n, const double* __restrict__ x, const int* __restrict__ mask,
+                                 double* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = x[i] * inv;
+    out[i] = mask[sg.node_prob[i / 7]] ? 0.0 : -x[i];
 }
 
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
@@ -122,83 +234,6 @@ __global__ void k_fill(int64_t n, double v, double* __restrict__ x) {
     x[i] = v;
 }
 
-// Hcol[k] = a[k] + b[k] (the two classical Gram-Schmidt passes)
-__global__ void k_add_small(int32_t nv, const double* __restrict__ a, const double* __restrict__ b,
-                            double* __restrict__ out, const int* guard) {
-  if (off(guard)) return;
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) out[k] = a[k] + b[k];
-}
-
-// start of a cycle: g = beta e_1 (beta = *scal), the cycle is active, no columns yet
-__global__ void k_cycle_init(double* __restrict__ g, int32_t ldh, const double* __restrict__ scal,
-                             int* __restrict__ active, int* __restrict__ kcols) {
-  for (int k = threadIdx.x; k < ldh; k += blockDim.x) g[k] = k == 0 ? *scal : 0.0;
-  if (threadIdx.x == 0) {
-    *active = 1;
-    *kcols = 0;
-  }
-}
-
-// Givens update of Hessenberg column j (column-major, leading dimension ldh):
-// apply the previous rotations, form the one that zeroes H[j+1][j], rotate the
-// right-hand side g; |g[j+1]| is the GMRES residual norm. Stops the cycle when
-// it reaches *target or the Krylov space is exhausted (H[j+1][j] = 0).
-__global__ void k_givens(double* __restrict__ H, int32_t ldh, int32_t j, double* __restrict__ cs,
-                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ res,
-                         const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kcols) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (active && *active == 0) return;
-  double* h = H + (int64_t)j * ldh;
-  const double sub = h[j + 1];
-  for (int i = 0; i < j; ++i) {
-    const double a = h[i], b = h[i + 1];
-    h[i] = cs[i] * a + sn[i] * b;
-    h[i + 1] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = h[j], b = h[j + 1];
-  const double r = hypot(a, b);
-  double c = 1.0, sv = 0.0;
-  if (r > 0.0) {
-    c = a / r;
-    sv = b / r;
-  }
-  cs[j] = c;
-  sn[j] = sv;
-  h[j] = r;
-  h[j + 1] = 0.0;
-  const double gj = g[j];
-  g[j] = c * gj;
-  g[j + 1] = -sv * gj;
-  const double rn = fabs(g[j + 1]);
-  *res = rn;
-  if (kcols) *kcols = j + 1;
-  if (active && target && (!(rn > *target) || sub == 0.0)) *active = 0;
-}
-
-// y = R^{-1} g for the k x k upper-triangular rotated Hessenberg R (k = *kdev if given)
-__global__ void k_lsq(const double* __restrict__ H, int32_t ldh, int32_t k, const int* __restrict__ kdev,
-                      const double* __restrict__ g, double* __restrict__ y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (kdev) k = *kdev;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int jj = i + 1; jj < k; ++jj) s -= H[(int64_t)jj * ldh + i] * y[jj];
-    const double d = H[(int64_t)i * ldh + i];
-    y[i] = d != 0.0 ? s / d : 0.0;
-  }
-}
-
-// x += sum_{q < k} y_q Z_q
-__global__ void k_update_x(int64_t n, const double* __restrict__ Z, int64_t ldz, const double* __restrict__ y,
-                           const int* __restrict__ kdev, double* __restrict__ x) {
-  const int k = *kdev;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = x[i];
-    for (int q = 0; q < k; ++q) s += y[q] * Z[(int64_t)q * ldz + i];
-    x[i] = s;
-  }
-}
-
 inline int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
   const int64_t cap = 152 * 32;
@@ -207,26 +242,63 @@ inline int grid_for(int64_t work, int block) {
 
 }  // namespace
 
-void launch_mdot(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                 double* out, const int* guard, cudaStream_t s) {
-  dim3 grid(RED_BLOCKS, (nv + MD - 1) / MD);
-  k_mdot<<<grid, RB, 0, s>>>(n, nv, V, ldv, w, partial, nv, guard);
-  k_reduce_partials<<<1, RB, 0, s>>>(nv, partial, nv, RED_BLOCKS, out, 0, guard);
+void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
+                     double* out, int32_t ldo, const int* guard, cudaStream_t s) {
+  dim3 grid((unsigned)sg.n_chunks, (nv + MD - 1) / MD);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, nv, V, ldv, w, partial, nv, guard);
+  k_seg_reduce<<<sg.P, 256, 0, s>>>(sg, nv, partial, nv, out, ldo, 0, guard);
 }
 
-void launch_maxpy(int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h, double* w,
-                  const int* guard, cudaStream_t s) {
-  k_maxpy<<<grid_for(n, 256), 256, 0, s>>>(n, nv, V, ldv, h, w, guard);
+void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
+                     const int* guard, cudaStream_t s) {
+  dim3 grid((unsigned)sg.n_chunks, 1);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, 1, guard);
+  k_seg_reduce<<<sg.P, 32, 0, s>>>(sg, 1, partial, 1, out, ldo, 1, guard);
 }
 
-void launch_norm(int64_t n, const double* x, double* partial, double* out, const int* guard, cudaStream_t s) {
-  k_norm_partial<<<RED_BLOCKS, RB, 0, s>>>(n, x, partial, guard);
-  k_reduce_partials<<<1, RB, 0, s>>>(1, partial, 1, RED_BLOCKS, out, 1, guard);
+void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,
+                      int32_t ldh, double* w, const int* guard, cudaStream_t s) {
+  k_seg_maxpy<<<grid_for(n, 256), 256, 0, s>>>(sg, n, nv, V, ldv, h, ldh, w, guard);
 }
 
-void launch_scale_inv(int64_t n, const double* x, const double* scal, double* y, const int* guard,
-                      cudaStream_t s) {
-  k_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(n, x, scal, y, guard);
+void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const double* scal, int32_t lds,
+                          double* y, const int* guard, cudaStream_t s) {
+  k_seg_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(sg, n, x, scal, lds, y, guard);
+}
+
+void launch_seg_add(int32_t P, int32_t nv, const double* a, const double* b, int32_t lda, double* H, int32_t ldHp,
+                    int64_t colofs, const int* guard, cudaStream_t s) {
+  k_seg_add<<<grid_for((int64_t)P * nv, 128), 128, 0, s>>>(P, nv, a, b, lda, H, ldHp, colofs, guard);
+}
+
+void launch_seg_cycle_init(int32_t P, double* g, int32_t ldg, const double* beta, const double* target, int* active,
+                           int* kcols, int* any, cudaStream_t s) {
+  k_seg_cycle_init<<<1, 256, 0, s>>>(P, g, ldg, beta, target, active, kcols, any);
+}
+
+void launch_seg_givens(int32_t P, double* H, int32_t ldh, int32_t m, int32_t j, double* cs, double* sn, double* g,
+                       double* res, const double* target, int* active, int* kcols, int* any, cudaStream_t s) {
+  k_seg_givens<<<1, 256, 0, s>>>(P, H, ldh, m, j, cs, sn, g, res, target, active, kcols, any);
+}
+
+void launch_seg_lsq(int32_t P, const double* H, int32_t ldh, int32_t m, const int* kcols, const double* g, double* y,
+                    cudaStream_t s) {
+  k_seg_lsq<<<(P + 63) / 64, 64, 0, s>>>(P, H, ldh, m, kcols, g, y);
+}
+
+void launch_seg_update_x(const SegDev& sg, int64_t n, const double* Z, int64_t ldz, const double* y, int32_t m,
+                         const int* kcols, double* x, cudaStream_t s) {
+  k_seg_update_x<<<grid_for(n, 256), 256, 0, s>>>(sg, n, Z, ldz, y, m, kcols, x);
+}
+
+void launch_seg_axpy(const SegDev& sg, int64_t n, const double* x, const double* alpha, const double* y, double* out,
+                     cudaStream_t s) {
+  k_seg_axpy<<<grid_for(n, 256), 256, 0, s>>>(sg, n, x, alpha, y, out);
+}
+
+void launch_seg_neg_masked(const SegDev& sg, int64_t n, const double* x, const int* mask, double* out,
+                           cudaStream_t s) {
+  k_seg_neg_masked<<<grid_for(n, 256), 256, 0, s>>>(sg, n, x, mask, out);
 }
 
 void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
@@ -239,29 +311,6 @@ void launch_copy(int64_t n, const double* x, double* y, cudaStream_t s) {
 
 void launch_fill(int64_t n, double v, double* x, cudaStream_t s) {
   k_fill<<<grid_for(n, 256), 256, 0, s>>>(n, v, x);
-}
-
-void launch_add_small(int32_t nv, const double* a, const double* b, double* out, const int* guard, cudaStream_t s) {
-  k_add_small<<<1, 64, 0, s>>>(nv, a, b, out, guard);
-}
-
-void launch_cycle_init(double* g, int32_t ldh, const double* scal, int* active, int* kcols, cudaStream_t s) {
-  k_cycle_init<<<1, 64, 0, s>>>(g, ldh, scal, active, kcols);
-}
-
-void launch_givens(double* H, int32_t ldh, int32_t j, double* cs, double* sn, double* g, double* res,
-                   const double* target, int* active, int* kcols, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, res, target, active, kcols);
-}
-
-void launch_lsq(const double* H, int32_t ldh, int32_t k, const int* kdev, const double* g, double* y,
-                cudaStream_t s) {
-  k_lsq<<<1, 32, 0, s>>>(H, ldh, k, kdev, g, y);
-}
-
-void launch_update_x(int64_t n, const double* Z, int64_t ldz, const double* y, const int* kdev, double* x,
-                     cudaStream_t s) {
-  k_update_x<<<grid_for(n, 256), 256, 0, s>>>(n, Z, ldz, y, kdev, x);
 }
 
 }  // namespace fsi

@@ -141,115 +141,21 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
   __syncwarp();
 }
 
-// Batched level-scheduled block ILU: grid = one CTA per subdomain (up to FW
-// warps); a warp factors one row of the current level entirely in its own
-// shared-memory slice: the row, the inverted pivots D_k of its L blocks and
-// every source block A_kj of its updates belong to finished rows, so they are
-// fetched together (one memory round trip per row); then for each L block
-// (i,k) in column order A_ik <- A_ik D_k^{-1} and all its updates
-// A_ij -= A_ik A_kj run from shared memory (lane task = update x column).
-// Levels are separated by __syncthreads.
-constexpr int FW = 4;
-
-// ALL = true: every source block of the row is fetched up front; false: the
-// sources of one L block at a time (rows too long for the whole set).
-template <class TF, bool ALL>
-__global__ void __launch_bounds__(32 * FW) k_ras_factor(RasDev R, TF* __restrict__ fac, int32_t* err) {
-  extern __shared__ __align__(16) unsigned char fsm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  const int32_t nsrc = ALL ? R.max_row_upd : R.max_entry_upd;
-  const size_t per = (size_t)(R.max_row_blocks + R.max_row_lent + nsrc) * 49 + 98;
-  TF* sRow = reinterpret_cast<TF*>(fsm) + (size_t)warp * per;
-  TF* sD = sRow + (size_t)R.max_row_blocks * 49;
-  TF* sSrc = sD + (size_t)R.max_row_lent * 49;
-  TF* sAug = sSrc + (size_t)nsrc * 49;
-  const int s = blockIdx.x;
-  const int64_t r0 = R.sd_row[s];
-  for (int64_t l = R.sd_lvlL[s]; l < R.sd_lvlL[s + 1]; ++l) {
-    const int64_t lb = R.lvlL_ptr[l], le = R.lvlL_ptr[l + 1];
-    for (int64_t ri = lb + warp; ri < le; ri += nw) {
-      const int64_t q = r0 + R.lvlL_rows[ri];
-      const int64_t rp = R.row_ptr[q];
-      const int nblk = (int)(R.row_ptr[q + 1] - rp);
-      const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
-      const int64_t u0 = R.upd_ptr[e0], u1 = R.upd_ptr[e1];
-      const int nl = (int)(e1 - e0), nu = (int)(u1 - u0);
-      for (int idx = lane; idx < 49 * nblk; idx += 32) sRow[idx] = fac[49 * rp + idx];
-      for (int idx = lane; idx < 49 * nl; idx += 32) {
-        const int e = idx / 49;
-        sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
-      }
-      if (ALL)
-        for (int idx = lane; idx < 49 * nu; idx += 32) {
-          const int u = idx / 49;
-          sSrc[idx] = fac[49 * R.upd_src[u0 + u] + (idx - 49 * u)];
-        }
-      __syncwarp();
-      for (int64_t e = e0; e < e1; ++e) {
-        TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
-        const TF* Dk = sD + 49 * (e - e0);
-        const int64_t us = ALL ? u0 : R.upd_ptr[e];
-        if (!ALL) {
-          const int ne = (int)(R.upd_ptr[e + 1] - us);
-          for (int idx = lane; idx < 49 * ne; idx += 32) {
-            const int u = idx / 49;
-            sSrc[idx] = fac[49 * R.upd_src[us + u] + (idx - 49 * u)];
-          }
-        }
-        // A_ik <- A_ik D_k^{-1}
-        TF v0 = TF(0), v1 = TF(0);
-        {
-          const int r_0 = lane / 7, c_0 = lane - 7 * r_0;
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) v0 += Aik[7 * r_0 + mm] * Dk[7 * mm + c_0];
-          if (lane + 32 < 49) {
-            const int e1_ = lane + 32, r_1 = e1_ / 7, c_1 = e1_ - 7 * r_1;
-#pragma unroll
-            for (int mm = 0; mm < 7; ++mm) v1 += Aik[7 * r_1 + mm] * Dk[7 * mm + c_1];
-          }
-        }
-        __syncwarp();
-        Aik[lane] = v0;
-        if (lane + 32 < 49) Aik[lane + 32] = v1;
-        __syncwarp();
-        // A_ij -= A_ik A_kj for every update of this L block: task = (update, column)
-        const int64_t ub = R.upd_ptr[e];
-        const int ntask = 7 * (int)(R.upd_ptr[e + 1] - ub);
-        for (int t = lane; t < ntask; t += 32) {
-          const int u = t / 7, cc = t - 7 * u;
-          TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
-          const TF* Akj = sSrc + 49 * (ub + u - us) + cc;
-          TF col[7];
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
-#pragma unroll
-          for (int rr = 0; rr < 7; ++rr) {
-            TF acc = Aij[7 * rr];
-#pragma unroll
-            for (int mm = 0; mm < 7; ++mm) acc -= Aik[7 * rr + mm] * col[mm];
-            Aij[7 * rr] = acc;
-          }
-        }
-        __syncwarp();
-      }
-      warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
-      for (int idx = lane; idx < 49 * nblk; idx += 32) fac[49 * rp + idx] = sRow[idx];
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-}
-
 // Batched block ILU, whole CTA on one row: one CTA per subdomain walks its rows
 // in increasing order (a topological order of the elimination). At the start
-// of a row the row itself and the inverted pivots D_k of its L blocks (finished
-// rows) are loaded into shared memory; the source blocks A_kj of the updates of
-// each L block arrive by cp.async into a double buffer, one L block ahead, so
-// their memory latency hides behind the previous L block's arithmetic. For each
-// L block (i,k): threads 0..48 form A_ik D_k^{-1} (into a separate buffer and
-// the row), then all threads apply its updates A_ij -= A_ik A_kj (task =
-// update x column) - two barriers per L block.
+// of a row the row itself is loaded into shared memory. For each L block (i,k):
+// threads 0..48 form A_ik D_k^{-1} (D_k: the inverted pivot of the finished row
+// k; into a separate buffer and the row), then all threads apply its updates
+// A_ij -= A_ik A_kj (task = update x column) - two barriers per L block.
+// MODE picks how much besides the row lives in shared memory, largest first:
+//   0: the pivots D_k of all L blocks of the row, loaded with the row, and the
+//      source blocks A_kj of each L block's updates in a cp.async double
+//      buffer, one L block ahead (their latency hides behind the previous L
+//      block's arithmetic);
+//   1: as 0 but D_k read from global memory (L2) when used;
+//   2: only the row: D_k and the sources read from global memory when used.
+// The host takes the first mode whose footprint fits (rows of high-fill ILU
+// in FP64 need the leaner ones).
 template <class TF>
 __device__ __forceinline__ void cp_async_elem(TF* dst, const TF* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -269,13 +175,13 @@ __device__ __forceinline__ void fetch_sources(const RasDev& R, const TF* fac, in
   }
 }
 
-template <class TF>
+template <class TF, int MODE>
 __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict__ fac, int32_t* err) {
   extern __shared__ __align__(16) unsigned char fsm[];
-  const size_t me = (size_t)R.max_entry_upd * 49;
+  const size_t me = MODE <= 1 ? (size_t)R.max_entry_upd * 49 : 0;
   TF* sRow = reinterpret_cast<TF*>(fsm);
   TF* sD = sRow + (size_t)R.max_row_blocks * 49;
-  TF* sSrc0 = sD + (size_t)R.max_row_lent * 49;
+  TF* sSrc0 = sD + (MODE == 0 ? (size_t)R.max_row_lent * 49 : 0);
   TF* sSrc1 = sSrc0 + me;
   TF* sScl = sSrc1 + me;
   TF* sAug = sScl + 49;
@@ -286,29 +192,34 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
     const int nblk = (int)(R.row_ptr[q + 1] - rp);
     const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
     const int nl = (int)(e1 - e0);
-    if (e0 < e1) fetch_sources<TF>(R, fac, e0, sSrc0, tid, nt);
-    cp_async_commit();
-    for (int idx = tid; idx < 49 * nblk; idx += nt) sRow[idx] = fac[49 * rp + idx];
-    for (int idx = tid; idx < 49 * nl; idx += nt) {
-      const int e = idx / 49;
-      sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
+    if (MODE <= 1) {
+      if (e0 < e1) fetch_sources<TF>(R, fac, e0, sSrc0, tid, nt);
+      cp_async_commit();
     }
+    for (int idx = tid; idx < 49 * nblk; idx += nt) sRow[idx] = fac[49 * rp + idx];
+    if (MODE == 0)
+      for (int idx = tid; idx < 49 * nl; idx += nt) {
+        const int e = idx / 49;
+        sD[idx] = fac[49 * R.lent_kdiag[e0 + e] + (idx - 49 * e)];
+      }
     __syncthreads();
     for (int64_t e = e0; e < e1; ++e) {
       TF* cur = ((e - e0) & 1) ? sSrc1 : sSrc0;
       TF* nxt = ((e - e0) & 1) ? sSrc0 : sSrc1;
-      if (e + 1 < e1) fetch_sources<TF>(R, fac, e + 1, nxt, tid, nt);
-      cp_async_commit();
+      if (MODE <= 1) {
+        if (e + 1 < e1) fetch_sources<TF>(R, fac, e + 1, nxt, tid, nt);
+        cp_async_commit();
+      }
       TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
       if (tid < 49) {
-        const TF* Dk = sD + 49 * (e - e0);
+        const TF* Dk = MODE == 0 ? sD + 49 * (e - e0) : fac + 49 * R.lent_kdiag[e];
         const int r = tid / 7, c = tid - 7 * r;
         TF v = TF(0);
 #pragma unroll
         for (int mm = 0; mm < 7; ++mm) v += Aik[7 * r + mm] * Dk[7 * mm + c];
         sScl[tid] = v;
       }
-      cp_async_wait1();  // this thread's copies of L block e have landed
+      if (MODE <= 1) cp_async_wait1();  // this thread's copies of L block e have landed
       __syncthreads();
       if (tid < 49) Aik[tid] = sScl[tid];
       const int64_t ub = R.upd_ptr[e];
@@ -316,7 +227,7 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
       for (int t = tid; t < ntask; t += nt) {
         const int u = t / 7, cc = t - 7 * u;
         TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
-        const TF* Akj = cur + 49 * u + cc;
+        const TF* Akj = (MODE <= 1 ? cur + 49 * u : fac + 49 * R.upd_src[ub + u]) + cc;
         TF col[7];
 #pragma unroll
         for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
@@ -441,50 +352,44 @@ void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s
 }
 
 template <class TF>
-size_t ras_factor_smem_per_warp(const RasDev& r, bool all) {
-  return ((size_t)(r.max_row_blocks + r.max_row_lent + (all ? r.max_row_upd : r.max_entry_upd)) * 49 + 98) *
-         sizeof(TF);
-}
-
-// warps per factorisation CTA: up to FW, as many as the shared memory allows
-// (whole-row source prefetch whenever one warp's slice fits: one memory round
-// trip per row is worth more than extra warps waiting on a level barrier)
-template <class TF>
-int ras_factor_warps(const RasDev& r, bool* all_out) {
-  const size_t budget = 200 * 1024;
-  bool all = ras_factor_smem_per_warp<TF>(r, true) <= budget;
-  int nw = (int)(budget / ras_factor_smem_per_warp<TF>(r, all));
-  if (all_out) *all_out = all;
-  return nw < 1 ? 0 : (nw > FW ? FW : nw);
+size_t ras_factor_cta_smem(const RasDev& r, int mode) {
+  size_t blocks = (size_t)r.max_row_blocks + 1;  // the row and the scaled L block
+  if (mode == 0) blocks += (size_t)r.max_row_lent + 2 * (size_t)r.max_entry_upd;
+  if (mode == 1) blocks += 2 * (size_t)r.max_entry_upd;
+  return (blocks * 49 + 98) * sizeof(TF);  // + the 7 x 14 inversion scratch
 }
 
 template <class TF>
-size_t ras_factor_cta_smem(const RasDev& r) {
-  return ((size_t)(r.max_row_blocks + r.max_row_lent + 2 * r.max_entry_upd + 1) * 49 + 98) * sizeof(TF);
+int ras_factor_mode(const RasDev& r, size_t* smem) {
+  for (int mode = 0; mode < 3; ++mode) {
+    const size_t b = ras_factor_cta_smem<TF>(r, mode);
+    if (b <= (mode == 0 ? FACTOR_SMEM_PREFERRED : FACTOR_SMEM_MAX)) {
+      if (smem) *smem = b;
+      return mode;
+    }
+  }
+  return -1;
+}
+
+template <class TF, int MODE>
+void launch_factor_mode(const RasDev& r, TF* fac, int32_t* err, size_t smem, cudaStream_t s) {
+  cudaFuncSetAttribute(k_ras_factor_cta<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ras_factor_cta<TF, MODE><<<r.np, 256, smem, s>>>(r, fac, err);
 }
 
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
-  const size_t smc = ras_factor_cta_smem<TF>(r);
-  if (smc <= 200 * 1024) {
-    cudaFuncSetAttribute(k_ras_factor_cta<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-    k_ras_factor_cta<TF><<<r.np, 256, smc, s>>>(r, fac, err);
-    return;
-  }
-  bool all = true;
-  const int nw = ras_factor_warps<TF>(r, &all);
-  const size_t sm = (size_t)nw * ras_factor_smem_per_warp<TF>(r, all);
-  if (all) {
-    cudaFuncSetAttribute(k_ras_factor<TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ras_factor<TF, true><<<r.np, 32 * nw, sm, s>>>(r, fac, err);
-  } else {
-    cudaFuncSetAttribute(k_ras_factor<TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ras_factor<TF, false><<<r.np, 32 * nw, sm, s>>>(r, fac, err);
+  const size_t smem = ras_factor_cta_smem<TF>(r, r.factor_mode);
+  switch (r.factor_mode) {
+    case 0: launch_factor_mode<TF, 0>(r, fac, err, smem, s); break;
+    case 1: launch_factor_mode<TF, 1>(r, fac, err, smem, s); break;
+    case 2: launch_factor_mode<TF, 2>(r, fac, err, smem, s); break;
+    default: break;  // fsi_create rejects such plans
   }
 }
 
-template int ras_factor_warps<float>(const RasDev&, bool*);
-template int ras_factor_warps<double>(const RasDev&, bool*);
+template int ras_factor_mode<float>(const RasDev&, size_t*);
+template int ras_factor_mode<double>(const RasDev&, size_t*);
 
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,

@@ -47,7 +47,8 @@ class FsiOptions(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int32), ("gmres_maxit", ctypes.c_int32),
                 ("n_subdomains", ctypes.c_int32), ("overlap", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("jac_lag", ctypes.c_int32), ("ilu_level", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
-                ("ordering", ctypes.c_int32), ("verbose", ctypes.c_int32), ("fault_test", ctypes.c_int32)]
+                ("ordering", ctypes.c_int32), ("factor_mode", ctypes.c_int32),
+                ("verbose", ctypes.c_int32), ("fault_test", ctypes.c_int32)]
 
 
 class FsiSolveStats(ctypes.Structure):

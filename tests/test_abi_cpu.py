@@ -32,6 +32,8 @@ def test_default_options_and_argument_errors():
     o = fsi.fsi_default_options()
     assert o.dt == 1e-3 and o.newton_rtol == 1e-6 and o.gmres_rtol == 1e-3
     assert o.gmres_restart == 30 and o.n_subdomains == 64 and o.overlap == 1 and o.precision == 0
+    # the fields after them line up with the C struct (a shifted layout would misread these)
+    assert (o.ilu_level, o.threads_per_row, o.ordering, o.factor_mode, o.verbose, o.fault_test) == (1, 32, 1, 0, 0, 0)
     L = fsi.lib()
     # null arguments are rejected before any device work
     assert L.fsi_create(None, None, None, 1, None, None, None) == 1

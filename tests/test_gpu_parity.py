@@ -198,3 +198,23 @@ def test_newton_steps_mixed_match_oracle(tube0, oracle_tube0_steps):
         rel = rel_by_group(y, ref[k])
         assert st.converged == 1
         assert all(v < 1e-6 for v in rel.values()), (k, rel)
+
+
+@pytest.mark.parametrize("precision,ilu", [(0, 1), (1, 2)])
+def test_factor_shared_memory_modes_are_bitwise_identical(tube0, precision, ilu):
+    """The three shared-memory modes of the ILU factorisation (pivots and
+    sources prefetched / sources only / neither) do the same arithmetic in the
+    same order, so the preconditioner applies agree bit for bit."""
+    y = vm.poiseuille_state(tube0)
+    r = torch.randn((tube0.n_nodes, 7), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    outs = []
+    for mode in (1, 2, 3):
+        S = make_solver(tube0, precision=precision, ilu_level=ilu, n_subdomains=4, factor_mode=mode)
+        S.set_state(y, t=0.0)
+        S.jacobian(y)
+        z = S.vec()
+        fsi.fsi_pc_apply(S.ctx, r, z)
+        outs.append(z.cpu().numpy())
+        S.close()
+    assert np.isfinite(outs[0]).all()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
