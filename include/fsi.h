@@ -125,11 +125,11 @@ typedef struct {
                              (global node order), 1 RCM, 2 RCM with lumen nodes
                              before interface and wall nodes */
   int32_t factor_mode;    /* shared-memory use of the ILU factorisation: 0 automatic
-                             (the most prefetching that fits); 1 pivots and update
-                             sources prefetched, 2 sources only, 3 neither (the row
-                             alone in shared memory). A forced mode that needs more
-                             shared memory than the automatic choice is FSI_ERR_ARG.
-                             All modes give bitwise identical factors. */
+                             (= 3, the fastest measured); 1 pivots and update sources
+                             prefetched into shared memory, 2 sources only, 3 neither
+                             (the row alone in shared memory). A forced mode whose
+                             footprint does not fit is FSI_ERR_ARG. All modes give
+                             bitwise identical factors. */
   int32_t verbose;        /* print per-iteration norms to stderr */
   int32_t fault_test;     /* tests only: 1 = the preconditioner apply's copy engine
                              issues nothing, so the apply's bounded wait runs out and

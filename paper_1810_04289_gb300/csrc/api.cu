@@ -743,14 +743,11 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rd.max_row_lent = (int32_t)ml;
       rd.max_row_upd = (int32_t)mu;
       rd.max_entry_upd = (int32_t)me;
-      const int fm = cp->mixed ? ras_factor_mode<float>(rd, nullptr) : ras_factor_mode<double>(rd, nullptr);
-      if (fm >= 0 && o.factor_mode > 0) {
-        if (o.factor_mode - 1 < fm) throw StatusError{FSI_ERR_ARG, "factor_mode needs more shared memory than fits"};
-        rd.factor_mode = o.factor_mode - 1;
-      } else {
-        rd.factor_mode = fm;
-      }
-      if (fm < 0) {
+      const int want = o.factor_mode > 0 ? o.factor_mode - 1 : 2;
+      auto fits = [&](int mode) { return cp->mixed ? ras_factor_fits<float>(rd, mode) : ras_factor_fits<double>(rd, mode); };
+      rd.factor_mode = want;
+      if (fits(2) && !fits(want)) throw StatusError{FSI_ERR_ARG, "factor_mode needs more shared memory than fits"};
+      if (!fits(2)) {
         char msg[192];
         std::snprintf(msg, sizeof msg,
                       "ILU rows too long for the shared-memory factorisation (%d blocks in the longest row; "
@@ -768,7 +765,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
 
     // packed factor streams for the TMA-fed apply
     {
-      std::vector<int64_t> Lcnt(R.gnode.size()), Ucnt(R.gnode.size()), Loff(R.np), Uoff(R.np), Lsrc, Usrc;
+      std::vector<int64_t> Lcnt(R.gnode.size()), Ucnt(R.gnode.size()), Loff(R.np + 1), Uoff(R.np + 1), Lsrc, Usrc;
       std::vector<int32_t> Lcol, Ucol;
       int64_t maxblk = 1;
       for (int32_t sd = 0; sd < R.np; ++sd) {
@@ -794,6 +791,8 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
           maxblk = std::max(maxblk, Ucnt[q]);
         }
       }
+      Loff[R.np] = (int64_t)Lsrc.size();
+      Uoff[R.np] = (int64_t)Usrc.size();
       RasStreamDev& rs = cp->rs;
       rs.np = R.np;
       rs.sd_row = rd.sd_row;
@@ -809,70 +808,27 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Lcol = cp->upload(Lcol);
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
-      // stage geometry: FSI_STAGE_BLOCKS / FSI_STAGES override the defaults (tuning)
-      int64_t sbdef = cp->mixed ? 64 : 32;
-      int nst = 2;
-      if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) sbdef = std::max(1, std::atoi(e));
+      // stage geometry: NST stages of SB blocks. The subdomains should all be
+      // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
+      // shared memory per CTA leaves after the vector; FSI_STAGE_BLOCKS /
+      // FSI_STAGES override (tuning)
+      const int vsz = cp->mixed ? 4 : 8, stride = cp->mixed ? 52 : 50;
+      int nst = 3;
+      const int64_t per_sm = std::min<int64_t>(8, (R.np + 151) / 152);
+      const int64_t fixed = 128 + 7 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
+      int64_t SB = ((int64_t)(227 * 1024) / per_sm - fixed) / (nst * stride * vsz);
+      SB = std::max<int64_t>(16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
+      if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) SB = std::max(1, std::atoi(e));
       if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));
-      const int64_t SB = std::max<int64_t>(maxblk, sbdef);
+      (void)maxblk;
       rs.nst = nst;
       rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
-      // row groups per stage
-      std::vector<int64_t> gLp{0}, gLb, gLn, gUp{0}, gUb, gUn;
-      std::vector<int32_t> gLr, gUr;
-      for (int32_t sd = 0; sd < R.np; ++sd) {
-        const int64_t a = R.sd_row[sd], b = R.sd_row[sd + 1];
-        int64_t blk = Loff[sd], n = 0;
-        gLr.push_back(0);
-        gLb.push_back(blk);
-        for (int64_t q = a; q < b; ++q) {
-          if (n > 0 && n + Lcnt[q] > SB) {
-            gLn.push_back(n);
-            blk += n;
-            n = 0;
-            gLr.push_back((int32_t)(q - a));
-            gLb.push_back(blk);
-          }
-          n += Lcnt[q];
-        }
-        gLn.push_back(n);
-        gLp.push_back((int64_t)gLr.size());
-        blk = Uoff[sd];
-        n = 0;
-        gUr.push_back((int32_t)(b - 1 - a));
-        gUb.push_back(blk);
-        for (int64_t q = b - 1; q >= a; --q) {
-          if (n > 0 && n + Ucnt[q] > SB) {
-            gUn.push_back(n);
-            blk += n;
-            n = 0;
-            gUr.push_back((int32_t)(q - a));
-            gUb.push_back(blk);
-          }
-          n += Ucnt[q];
-        }
-        gUn.push_back(n);
-        gUp.push_back((int64_t)gUr.size());
-      }
-      rs.gL_ptr = cp->upload(gLp);
-      rs.gL_row = cp->upload(gLr);
-      rs.gL_blk = cp->upload(gLb);
-      rs.gL_nblk = cp->upload(gLn);
-      rs.gU_ptr = cp->upload(gUp);
-      rs.gU_row = cp->upload(gUr);
-      rs.gU_blk = cp->upload(gUb);
-      rs.gU_nblk = cp->upload(gUn);
-      int64_t mg = 1;
-      for (int32_t sd = 0; sd < R.np; ++sd)
-        mg = std::max(mg, (gLp[sd + 1] - gLp[sd]) + (gUp[sd + 1] - gUp[sd]));
-      rs.max_groups = (int32_t)mg;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
       cp->use_stream = sm <= 200 * 1024;
       if (cp->use_stream) {
         CK(cp->mixed ? ras_stream_init<float>(rs) : ras_stream_init<double>(rs));
-        const int stride = cp->mixed ? 52 : 50;
         rs.Lpack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nL, 1));
         rs.Upack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nU, 1));
       }

@@ -83,10 +83,8 @@ void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
 template <class TF>
-int ras_factor_mode(const RasDev& r, size_t* smem);  // -1: a row does not fit in shared memory
-// shared-memory limits of the factorisation CTA: the prefetching mode is used
-// up to FACTOR_SMEM_PREFERRED, the leaner ones up to the opt-in maximum
-constexpr size_t FACTOR_SMEM_PREFERRED = 200 * 1024;
+bool ras_factor_fits(const RasDev& r, int mode);  // shared-memory mode 0..2 fits one CTA
+// shared-memory limit of the factorisation CTA (the opt-in maximum)
 constexpr size_t FACTOR_SMEM_MAX = 227 * 1024;
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,
@@ -100,8 +98,8 @@ struct RasStreamDev {
   const uint8_t* owned;
   const int64_t* L_cnt;   // [rows] L blocks of each row
   const int64_t* U_cnt;   // [rows] 1 (inverted pivot) + U blocks of each row
-  const int64_t* L_off;   // [np] first packed L block of each subdomain
-  const int64_t* U_off;   // [np] first packed U block of each subdomain
+  const int64_t* L_off;   // [np+1] first packed L block of each subdomain
+  const int64_t* U_off;   // [np+1] first packed U block of each subdomain
   void* Lpack;
   void* Upack;
   int64_t nL, nU;
@@ -109,18 +107,8 @@ struct RasStreamDev {
   const int32_t* Lcol;    // [nL] subdomain-relative column row
   const int64_t* Usrc;
   const int32_t* Ucol;
-  int32_t stage_blocks;   // blocks per ring stage (>= the longest row)
+  int32_t stage_blocks;   // blocks per ring stage (one bulk copy; rows may straddle stages)
   int64_t max_rows;       // rows of the largest subdomain
-  // row groups: consecutive rows whose blocks fit one stage, one bulk copy each
-  const int64_t* gL_ptr;  // [np+1] groups of each subdomain (L stream)
-  const int32_t* gL_row;  // [groups] first row (ascending; the group ends where the next starts)
-  const int64_t* gL_blk;  // [groups] first packed block
-  const int64_t* gL_nblk; // [groups] blocks in the group
-  const int64_t* gU_ptr;  // same for the U stream (rows descending)
-  const int32_t* gU_row;
-  const int64_t* gU_blk;
-  const int64_t* gU_nblk;
-  int32_t max_groups;     // most L + U groups of one subdomain
   int32_t nst;            // ring stages in flight (2..8)
   int32_t stall;          // tests only: the producer issues nothing (bounded waits run out)
 };

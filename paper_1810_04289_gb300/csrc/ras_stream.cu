@@ -1,19 +1,23 @@
 // Streamed RAS apply (Sec. 3, Eq. 16) for GB300: one CTA per subdomain, two
 // warps. Warp 1 (one elected lane) is a producer that streams the packed factor
-// rows with 1-D bulk copies (cp.async.bulk, the TMA engine) into a ring of
+// with 1-D bulk copies (cp.async.bulk, the TMA engine) into a ring of
 // shared-memory stages guarded by mbarriers; warp 0 is the consumer that walks
 // the rows in order (forward solve with the unit lower factor, then backward
 // solve with the upper factor and inverted pivots) on the subdomain vector held
 // in shared memory. The dependency chain of an ILU solve on an RCM-ordered
 // subdomain is nearly the row count, so the rows are processed one after the
-// other by all 28 lanes (4 blocks at a time x 7 components) while the factor
-// bytes for the rows ahead are already in flight.
+// other by 28 lanes (4 blocks at a time x 7 components) while the factor bytes
+// for the rows ahead are already in flight.
 //
 // Packed layout (built by k_pack_factors after each factorisation):
 //   L stream: for every row in increasing order, its L blocks;
 //   U stream: for every row in decreasing order, its inverted pivot, then its U blocks.
 // Each packed block holds 49 values, then the subdomain-relative column row in
 // the first 4 bytes of slot 49, padded to a 16-byte multiple (52 floats, 50 doubles).
+// Stages are fixed slices of stage_blocks blocks of a subdomain's L stream, then
+// of its U stream; a row may straddle stages (its partial sums carry over), so
+// the stage size is independent of the row length and can be chosen for
+// occupancy.
 //
 // Every wait on an mbarrier is bounded; on timeout the kernel records
 // FSI_ERR_TIMEOUT-style status in *err, drains (bounded) and returns.
@@ -115,9 +119,6 @@ __device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w
   return acc;
 }
 
-// Each stage carries a group of consecutive rows of one stream (at most
-// stage_blocks blocks), so one bulk copy moves several rows and NST groups are
-// in flight ahead of the consumer.
 template <class TF>
 __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const double* __restrict__ rin,
                                                          double* __restrict__ z, float* __restrict__ z32,
@@ -126,25 +127,22 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
   constexpr int STR = Pack<TF>::stride;
   extern __shared__ __align__(128) unsigned char smem[];
   const int NST = R.nst;
+  const int SB = R.stage_blocks;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + NSTMAX;
   TF* ring = reinterpret_cast<TF*>(smem + 128);
-  TF* w = ring + (size_t)NST * R.stage_blocks * STR;
+  TF* w = ring + (size_t)NST * SB * STR;
   const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s];
   const int m = (int)(R.sd_row[s + 1] - r0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-row block counts of both streams and the group table, next to the vector
+  // per-row block counts of both streams, next to the vector
   unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 7 * (size_t)R.max_rows);
   unsigned short* Ucnt = Lcnt + R.max_rows;
-  int* grow = reinterpret_cast<int*>(Ucnt + R.max_rows);  // 4-byte aligned: 2 x max_rows shorts
-  int* gblk = grow + R.max_groups;
-  int* gnb = gblk + R.max_groups;
-  const int64_t gL0 = R.gL_ptr[s], gL1 = R.gL_ptr[s + 1];
-  const int64_t gU0 = R.gU_ptr[s], gU1 = R.gU_ptr[s + 1];
-  const int nGL = (int)(gL1 - gL0);
-  const int ngroups = nGL + (int)(gU1 - gU0);
   const int64_t Lb0 = R.L_off[s], Ub0 = R.U_off[s];
+  const int64_t nLb = R.L_off[s + 1] - Lb0, nUb = R.U_off[s + 1] - Ub0;
+  const int nGL = (int)((nLb + SB - 1) / SB);
+  const int ngroups = nGL + (int)((nUb + SB - 1) / SB);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NST; ++i) {
@@ -164,13 +162,6 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     Lcnt[q] = (unsigned short)R.L_cnt[r0 + q];
     Ucnt[q] = (unsigned short)R.U_cnt[r0 + q];
   }
-  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
-    const bool isL = g < nGL;
-    const int64_t gg = isL ? gL0 + g : gU0 + (g - nGL);
-    grow[g] = isL ? R.gL_row[gg] : R.gU_row[gg];
-    gblk[g] = (int)(isL ? R.gL_blk[gg] - Lb0 : R.gU_blk[gg] - Ub0);
-    gnb[g] = (int)(isL ? R.gL_nblk[gg] : R.gU_nblk[gg]);
-  }
   __syncthreads();
 
   const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack) + (size_t)Lb0 * STR;
@@ -184,12 +175,12 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
         const int st = it % NST;
         if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
         if (!ok) break;
-        const uint32_t bytes = (uint32_t)(gnb[it] * STR * sizeof(TF));
+        const bool isL = it < nGL;
+        const int64_t first = (int64_t)(isL ? it : it - nGL) * SB;
+        const int64_t nb = (isL ? nLb : nUb) - first;
+        const uint32_t bytes = (uint32_t)((nb < SB ? nb : SB) * STR * sizeof(TF));
         mbar_arrive_expect_tx(&full[st], bytes);
-        if (bytes) {
-          const TF* src = (it < nGL ? Lpack : Upack) + (size_t)gblk[it] * STR;
-          bulk_g2s(ring + (size_t)st * R.stage_blocks * STR, src, bytes, &full[st]);
-        }
+        bulk_g2s(ring + (size_t)st * SB * STR, (isL ? Lpack : Upack) + (size_t)first * STR, bytes, &full[st]);
       }
       if (!ok) atomicExch(err, 2);
       // drain: the last copy issued into each stage must land before the CTA
@@ -199,53 +190,110 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
     return;
   }
 
-  // consumer warp
+  // consumer warp. Per stage: finish the row that straddles in from the previous
+  // stage, then the rows that lie wholly inside the stage (the common case, no
+  // bookkeeping), then start the row that straddles out; its partial sum carries.
   const int j = lane / 7, c = lane - 7 * (lane / 7);  // block slot 0..3 (4 = idle), component
   bool ok = true;
   int it = 0;
   // forward: w_q -= sum_k L_qk w_k
-  for (; it < nGL && ok; ++it) {
-    const int st = it % NST;
-    ok = mbar_wait(&full[st], (it / NST) & 1);
-    if (!ok) break;
-    const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    const int qa = grow[it];
-    const int qend = (it + 1 < nGL) ? grow[it + 1] : m;   // exclusive, ascending
-    for (int q = qa; q < qend; ++q) {
-      const int nb = Lcnt[q];
-      const TF acc = row_dot<TF, STR>(stg, 0, nb, w, j, c);
-      if (lane < 7 && nb > 0) w[7 * q + lane] -= acc;
+  {
+    int q = 0, rem = 0;
+    TF acc = TF(0);
+    for (int g = 0; g < nGL; ++g, ++it) {
+      const int st = it % NST;
+      ok = mbar_wait(&full[st], (it / NST) & 1);
+      if (!ok) break;
+      const TF* stg = ring + (size_t)st * SB * STR;
+      const int cap = (int)min((int64_t)SB, nLb - (int64_t)g * SB);
+      int pos = 0;
+      if (rem > 0) {
+        const int k = min(rem, cap);
+        acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+        pos = k;
+        rem -= k;
+        if (rem == 0) {
+          if (lane < 7) w[7 * q + lane] -= acc;
+          __syncwarp();
+          ++q;
+        }
+      }
+      if (rem == 0) {
+        for (; q < m; ++q) {
+          const int nb = Lcnt[q];
+          if (pos + nb > cap) break;
+          const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
+          if (lane < 7 && nb > 0) w[7 * q + lane] -= a;
+          __syncwarp();
+          pos += nb;
+        }
+        if (q < m && pos < cap) {
+          acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
+          rem = Lcnt[q] - (cap - pos);
+        }
+      }
       __syncwarp();
-      stg += (size_t)nb * STR;
+      if (lane == 0) mbar_arrive(&empty[st]);
     }
-    if (lane == 0) mbar_arrive(&empty[st]);
   }
-  // backward: w_q = D_q^{-1} (w_q - sum_j U_qj w_j)
-  for (; it < ngroups && ok; ++it) {
-    const int st = it % NST;
-    ok = mbar_wait(&full[st], (it / NST) & 1);
-    if (!ok) break;
-    const TF* stg = ring + (size_t)st * R.stage_blocks * STR;
-    const int qa = grow[it];                                  // first (highest) row of the group
-    const int qend = (it + 1 < ngroups) ? grow[it + 1] : -1;  // exclusive, descending
-    for (int q = qa; q > qend; --q) {
-      const int nb = Ucnt[q];
-      const TF acc = row_dot<TF, STR>(stg, 1, nb, w, j, c);
-      const TF t = (lane < 7) ? w[7 * q + lane] - acc : TF(0);
+  // backward: w_q = D_q^{-1} (w_q - sum_j U_qj w_j); the pivot is the row's first block
+  if (ok) {
+    int q = m - 1, rem = 0;
+    TF acc = TF(0);
+    TF dreg[7];
+    auto finish = [&](int row, TF sum) {
+      const TF t = (lane < 7) ? w[7 * row + lane] - sum : TF(0);
       TF tv[7];
 #pragma unroll
       for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
       if (lane < 7) {
-        const TF* D = stg + 7 * lane;  // first block of the row: inverted pivot
         TF zz = TF(0);
 #pragma unroll
-        for (int mm = 0; mm < 7; ++mm) zz += D[mm] * tv[mm];
-        w[7 * q + lane] = zz;
+        for (int mm = 0; mm < 7; ++mm) zz += dreg[mm] * tv[mm];
+        w[7 * row + lane] = zz;
       }
       __syncwarp();
-      stg += (size_t)nb * STR;
+    };
+    auto load_pivot = [&](const TF* blk) {
+#pragma unroll
+      for (int mm = 0; mm < 7; ++mm) dreg[mm] = lane < 7 ? blk[7 * lane + mm] : TF(0);
+    };
+    for (; it < ngroups; ++it) {
+      const int st = it % NST;
+      ok = mbar_wait(&full[st], (it / NST) & 1);
+      if (!ok) break;
+      const TF* stg = ring + (size_t)st * SB * STR;
+      const int cap = (int)min((int64_t)SB, nUb - (int64_t)(it - nGL) * SB);
+      int pos = 0;
+      if (rem > 0) {
+        const int k = min(rem, cap);
+        acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+        pos = k;
+        rem -= k;
+        if (rem == 0) {
+          finish(q, acc);
+          --q;
+        }
+      }
+      if (rem == 0) {
+        for (; q >= 0; --q) {
+          const int nb = Ucnt[q];
+          if (pos + nb > cap) break;
+          const TF* rs = stg + (size_t)pos * STR;
+          load_pivot(rs);
+          finish(q, row_dot<TF, STR>(rs, 1, nb, w, j, c));
+          pos += nb;
+        }
+        if (q >= 0 && pos < cap) {
+          const TF* rs = stg + (size_t)pos * STR;
+          load_pivot(rs);
+          acc = row_dot<TF, STR>(rs, 1, cap - pos, w, j, c);
+          rem = Ucnt[q] - (cap - pos);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
     }
-    if (lane == 0) mbar_arrive(&empty[st]);
   }
   if (!ok) {
     if (lane == 0) atomicExch(err, 2);
@@ -297,7 +345,7 @@ __global__ void k_pack_factors(int64_t nL, const int64_t* __restrict__ Lsrc, con
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r) {
   return 128 + (size_t)r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) + (size_t)7 * r.max_rows * sizeof(TF) +
-         (size_t)4 * r.max_rows + 16 + (size_t)12 * r.max_groups;
+         (size_t)4 * r.max_rows + 16;
 }
 
 template <class TF>
@@ -311,6 +359,10 @@ void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s) {
 
 template <class TF>
 cudaError_t ras_stream_init(const RasStreamDev& r) {
+  // all of the unified L1/shared storage as shared memory: several CTAs per SM
+  cudaError_t e = cudaFuncSetAttribute(k_ras_apply_stream<TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ras_apply_stream<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ras_stream_smem<TF>(r));
 }

@@ -154,8 +154,8 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
 //      block's arithmetic);
 //   1: as 0 but D_k read from global memory (L2) when used;
 //   2: only the row: D_k and the sources read from global memory when used.
-// The host takes the first mode whose footprint fits (rows of high-fill ILU
-// in FP64 need the leaner ones).
+// All three do the same arithmetic in the same order (bitwise identical
+// factors); mode 2 is the default (see ras_factor_fits).
 template <class TF>
 __device__ __forceinline__ void cp_async_elem(TF* dst, const TF* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -359,20 +359,19 @@ size_t ras_factor_cta_smem(const RasDev& r, int mode) {
   return (blocks * 49 + 98) * sizeof(TF);  // + the 7 x 14 inversion scratch
 }
 
+// Fit check of a factorisation mode. The automatic choice is the leanest mode
+// (2): measured on GB300 it is the fastest, because the smaller footprint lets
+// more subdomain CTAs share an SM, which hides the latency of the pivot and
+// source reads better than prefetching them does.
 template <class TF>
-int ras_factor_mode(const RasDev& r, size_t* smem) {
-  for (int mode = 0; mode < 3; ++mode) {
-    const size_t b = ras_factor_cta_smem<TF>(r, mode);
-    if (b <= (mode == 0 ? FACTOR_SMEM_PREFERRED : FACTOR_SMEM_MAX)) {
-      if (smem) *smem = b;
-      return mode;
-    }
-  }
-  return -1;
+bool ras_factor_fits(const RasDev& r, int mode) {
+  return ras_factor_cta_smem<TF>(r, mode) <= FACTOR_SMEM_MAX;
 }
 
 template <class TF, int MODE>
 void launch_factor_mode(const RasDev& r, TF* fac, int32_t* err, size_t smem, cudaStream_t s) {
+  cudaFuncSetAttribute(k_ras_factor_cta<TF, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_ras_factor_cta<TF, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ras_factor_cta<TF, MODE><<<r.np, 256, smem, s>>>(r, fac, err);
 }
@@ -388,8 +387,8 @@ void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
   }
 }
 
-template int ras_factor_mode<float>(const RasDev&, size_t*);
-template int ras_factor_mode<double>(const RasDev&, size_t*);
+template bool ras_factor_fits<float>(const RasDev&, int);
+template bool ras_factor_fits<double>(const RasDev&, int);
 
 template <class TF>
 void launch_ras_apply(const RasDev& r, const TF* fac, const double* rin, TF* work, double* z, float* z32,
