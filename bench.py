@@ -191,7 +191,7 @@ def run_ours(args, rank, world):
             from paper_1810_04289_gb300.autotune import autotune
             t_tune = time.perf_counter()
             opt, table = autotune(m, MATERIAL, y0, base=opt)
-            tuned = {"chosen": {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level",
+            tuned = {"chosen": {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level", "ordering",
                                                              "threads_per_row")},
                      "seconds": time.perf_counter() - t_tune, "candidates": table}
         S = fsi.Solver(m, MATERIAL, opt)
@@ -388,6 +388,7 @@ def main():
                    "subdomains": head["info"]["n_subdomains"],
                    "overlap": (head["tuned"] or {}).get("chosen", {}).get("overlap", args.overlap),
                    "ilu": (head["tuned"] or {}).get("chosen", {}).get("ilu_level", args.ilu),
+                   "ordering": (head["tuned"] or {}).get("chosen", {}).get("ordering", 1),
                    "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol,
                    "l2": "working set (BSR + ILU factors) larger than L2 each step",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -15,11 +15,15 @@ import time
 from . import fsi
 
 def default_grid(n_nodes):
-    """Subdomain counts (powers of two) giving 80..1000 nodes per subdomain, ILU(1)
+    """Subdomain counts (powers of two) giving 40..1000 nodes per subdomain, ILU(1)
     and ILU(2) (the paper's defaults for its small and large meshes, Sec. 4.3,
-    4.7), overlap 1, one warp per SpMV block row."""
-    nps = [2 ** k for k in range(4, 16) if 80 <= n_nodes / 2 ** k <= 1000] or [max(1, n_nodes // 400)]
-    return dict(n_subdomains=tuple(nps), overlap=(1,), ilu_level=(1, 2), threads_per_row=(32,))
+    4.7), RCM and lumen-first RCM orderings inside the subdomains (on thin-walled
+    small tubes ILU(1) with plain RCM can stall where the lumen-first order
+    converges), overlap 1, one warp per SpMV block row. Small subdomains stay in the
+    grid because each subdomain's triangular solve is a sequential chain on the
+    GPU: more, shorter chains can win despite more Krylov iterations."""
+    nps = [2 ** k for k in range(4, 16) if 40 <= n_nodes / 2 ** k <= 1000] or [max(1, n_nodes // 400)]
+    return dict(n_subdomains=tuple(nps), overlap=(1,), ilu_level=(1, 2), ordering=(1, 2), threads_per_row=(32,))
 
 
 def _time_linear_system(S, y, torch):
