@@ -39,6 +39,13 @@ WORKLOADS = {
 MATERIAL = dict(rho_f=1.05, mu_f=0.035, rho_s=1.2, E_s=3.0e6, nu_s=0.45, eta_s=0.0)
 S_F64 = 8
 S_F32 = 4
+# DRAM bytes per launch (read + write) from one ncu capture of the kernel as it is
+# now, keyed by (workload, phase, precision, subdomains, ILU level, ordering);
+# the summary that holds the capture is named beside it
+NCU_TRAFFIC = {
+    ("tube-96x32x15", "pcapply", "mixed", 512, 1, 1): (585.6e6, "profiles/k_ras_apply_stream_tube-96x32x15.md"),
+    ("tube-96x32x15", "spmv", "mixed", 512, 1, 1): (142.7e6, "profiles/k_bsr_spmv_tube-96x32x15.md"),
+}
 
 
 def parse():
@@ -369,6 +376,13 @@ def main():
     dom = max((k for k in hp if "gbs" in hp[k]), key=lambda k: hp[k]["ms_total"])
     roof = {"kernel": dom, "bound": "hbm", "achieved": hp[dom]["gbs"], "peak": hbm_peak, "unit": "GB/s",
             "frac": hp[dom]["gbs"] / hbm_peak, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    hi = head["info"]
+    ch = (head["tuned"] or {}).get("chosen", {})
+    key = (args.workload, dom, "mixed" if "mixed" in res else "fp64", hi["n_subdomains"],
+           ch.get("ilu_level", args.ilu), ch.get("ordering", 1))
+    if key in NCU_TRAFFIC:
+        roof["traffic"], roof["traffic_source"] = NCU_TRAFFIC[key]
+        roof["algorithmic_bytes"] = hp[dom]["algorithmic_bytes_per_launch"]
     st = head["stats"]
     ni = float(np.mean([s["newton_iterations"] for s in st]))
     nres = float(np.mean([s["residual_evaluations"] for s in st]))
