@@ -212,7 +212,7 @@ void residual(fsi_ctx* c, const double* y, double* F) {
 
 // per-problem 2-norms of x into c->hvec (host); returns the norm over all problems
 double norms(fsi_ctx* c, const double* x, std::vector<double>& out) {
-  c->launches += 2;
+  c->launches += 1;
   launch_seg_norm(c->seg, x, c->partial, c->beta, 1, nullptr, c->s);
   out.resize(c->nprob);
   CK(cudaMemcpyAsync(c->hbuf, c->beta, sizeof(double) * c->nprob, cudaMemcpyDeviceToHost, c->s));
@@ -331,12 +331,12 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
   launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, guard, st);
-  launch_seg_add(P, j + 1, c->hA, c->hB, ldh, c->H, (int32_t)((int64_t)ldh * m), (int64_t)j * ldh, guard, st);
-  // H[p][j+1][j] = ||w_p||: norm into hA[p][0], copied into place by the Givens kernel's caller layout
+  // H[p][j+1][j] = ||w_p||, written in place (per-problem stride ldh * m), then w_p /= it
   launch_seg_norm(c->seg, w, c->partial, c->H + (int64_t)j * ldh + j + 1, ldh * m, guard, st);
   launch_seg_scale_inv(c->seg, n, w, c->H + (int64_t)j * ldh + j + 1, ldh * m, w, guard, st);
-  launch_seg_givens(P, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active, c->kcols, c->anyact, st);
-  c->launches += 10;
+  launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
+                    c->kcols, c->anyact, st);
+  c->launches += 6;
 }
 
 // The kernels of one restart cycle for every problem, from V_0 = r / ||r|| to
@@ -363,7 +363,7 @@ void cycle_kernels(fsi_ctx* c, cudaStream_t st) {
   spmv_on(c, c->dy, nullptr, c->r, nullptr, st);
   launch_axpby(n, 1.0, c->rhs, -1.0, c->r, c->r, st);
   launch_seg_norm(c->seg, c->r, c->partial, c->beta, 1, nullptr, st);
-  c->launches += 3;
+  c->launches += 2;
 }
 
 void build_graph(fsi_ctx* c) {
@@ -693,6 +693,8 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       cp->seg.prob_chunk = cp->upload(pc);
       cp->seg.node_prob = cp->nprobid;
       cp->partial = cp->dalloc<double>(cp->seg.n_chunks * (m + 1));
+      cp->seg.counter = cp->dalloc<int>(NP * SEG_GROUPS);
+      CK(cudaMemsetAsync(cp->seg.counter, 0, sizeof(int) * NP * SEG_GROUPS, cp->s));
     }
     cp->beta = cp->dalloc<double>(n_problems);
     cp->gres = cp->dalloc<double>(n_problems);

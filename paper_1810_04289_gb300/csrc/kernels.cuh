@@ -134,7 +134,9 @@ struct SegDev {
   const int64_t* chunk_beg;  // [n_chunks+1] first dof of each chunk (chunks never straddle problems)
   const int64_t* prob_chunk; // [P+1] chunks of each problem
   const int32_t* node_prob;  // [N] problem of each node
+  int* counter;              // [P * SEG_GROUPS] blocks done per (problem, vector group); zero between launches
 };
+constexpr int SEG_GROUPS = 9;  // vector groups of 8 in one multi-dot (restart <= 64 -> at most 65 vectors)
 void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
                      double* out, int32_t ldo, const int* guard, cudaStream_t s);
 void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
@@ -143,12 +145,14 @@ void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, 
                       int32_t ldh, double* w, const int* guard, cudaStream_t s);
 void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const double* scal, int32_t lds,
                           double* y, const int* guard, cudaStream_t s);
-void launch_seg_add(int32_t P, int32_t nv, const double* a, const double* b, int32_t lda, double* H, int32_t ldHp,
-                    int64_t colofs, const int* guard, cudaStream_t s);
+
 void launch_seg_cycle_init(int32_t P, double* g, int32_t ldg, const double* beta, const double* target, int* active,
                            int* kcols, int* any, cudaStream_t s);
-void launch_seg_givens(int32_t P, double* H, int32_t ldh, int32_t m, int32_t j, double* cs, double* sn, double* g,
-                       double* res, const double* target, int* active, int* kcols, int* any, cudaStream_t s);
+// column j of each active problem's Hessenberg = a + b (the two Gram-Schmidt passes, lda apart per
+// problem), then the Givens update
+void launch_seg_givens(int32_t P, const double* a, const double* b, int32_t lda, double* H, int32_t ldh, int32_t m,
+                       int32_t j, double* cs, double* sn, double* g, double* res, const double* target, int* active,
+                       int* kcols, int* any, cudaStream_t s);
 void launch_seg_lsq(int32_t P, const double* H, int32_t ldh, int32_t m, const int* kcols, const double* g, double* y,
                     cudaStream_t s);
 void launch_seg_update_x(const SegDev& sg, int64_t n, const double* Z, int64_t ldz, const double* y, int32_t m,

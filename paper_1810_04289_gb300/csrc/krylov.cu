@@ -1,8 +1,10 @@
 // FP64 vector kernels of the batched Krylov loop. The unknowns of P independent
 // problems are stored one after the other; every reduction is segmented by
 // problem: a fixed table of chunks (each inside one problem) is reduced by one
-// block per chunk, then each problem sums its chunks in fixed order, so results
-// are bitwise reproducible run to run and independent problems never mix.
+// block per chunk, and the last block of a problem to finish (a per-problem
+// counter) sums that problem's chunk partials in fixed order, so results are
+// bitwise reproducible run to run, independent problems never mix, and a
+// reduction is one launch.
 // Per-problem Arnoldi scalars: H (column-major (m+1) x m per problem), g, Givens
 // cs/sn, residual estimates, stop flags.
 //
@@ -28,12 +30,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[c * ldp + k] = sum over chunk c of V_k . w (V_k = w itself if V is null: squared norm)
+// out[p * ldo + k] = sum over the dofs of problem p of V_k . w (V null: w . w,
+// and take_sqrt gives the 2-norm). Block (c, y) forms the partials of chunk c
+// for vectors 8y .. 8y+7; the last block of problem p for group y sums the
+// problem's partials (one warp per vector, lanes over the chunks in fixed order)
+// and resets the counter.
 __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const double* __restrict__ V, int64_t ldv,
                                                  const double* __restrict__ w, double* __restrict__ partial,
-                                                 int32_t ldp, const int* guard) {
+                                                 double* __restrict__ out, int32_t ldo, int take_sqrt,
+                                                 const int* guard) {
   if (off(guard)) return;
   __shared__ double red[MD][RB / 32];
+  __shared__ int s_last;
   const int c = blockIdx.x;
   const int k0 = blockIdx.y * MD;
   const int64_t i0 = sg.chunk_beg[c], i1 = sg.chunk_beg[c + 1];
@@ -56,24 +64,26 @@ __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const do
   if (threadIdx.x < MD && k0 + threadIdx.x < nv) {
     double v = 0.0;
     for (int q = 0; q < RB / 32; ++q) v += red[threadIdx.x][q];
-    partial[(int64_t)c * ldp + k0 + threadIdx.x] = v;
+    partial[(int64_t)c * nv + k0 + threadIdx.x] = v;
   }
-}
-
-// out[p * ldo + k] = sum over the chunks of problem p of partial[c * ldp + k]:
-// one block per problem, one warp per k, lanes over the chunks (fixed order)
-__global__ void k_seg_reduce(SegDev sg, int32_t nv, const double* __restrict__ partial, int32_t ldp,
-                             double* __restrict__ out, int32_t ldo, int take_sqrt, const int* guard) {
-  if (off(guard)) return;
-  const int p = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // publish the partials, then count this block in
+  __threadfence();
+  __syncthreads();
+  const int p = sg.node_prob[i0 / 7];
   const int64_t c0 = sg.prob_chunk[p], c1 = sg.prob_chunk[p + 1];
-  for (int k = warp; k < nv; k += nw) {
+  int* cnt = sg.counter + (int64_t)p * SEG_GROUPS + blockIdx.y;
+  if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1) == (int)(c1 - c0) - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int k = k0 + warp;
+  if (warp < MD && k < nv) {
     double v = 0.0;
-    for (int64_t c = c0 + lane; c < c1; c += 32) v += partial[c * ldp + k];
+    for (int64_t cc = c0 + lane; cc < c1; cc += 32) v += __ldcg(partial + cc * nv + k);
     v = warp_sum(v);
     if (lane == 0) out[(int64_t)p * ldo + k] = take_sqrt ? sqrt(v) : v;
   }
+  if (threadIdx.x == 0) *cnt = 0;
 }
 
 // w_i -= sum_k h[p(i)][k] V_k[i]
@@ -98,18 +108,6 @@ __global__ void k_seg_scale_inv(SegDev sg, int64_t n, const double* __restrict__
   }
 }
 
-// H[p][:, j] = a[p] + b[p] (the two classical Gram-Schmidt passes), first j+1 entries
-__global__ void k_seg_add(int32_t P, int32_t nv, const double* __restrict__ a, const double* __restrict__ b,
-                          int32_t lda, double* __restrict__ H, int32_t ldHp, int64_t colofs, const int* guard) {
-  if (off(guard)) return;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)P * nv;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = idx / nv;
-    const int k = (int)(idx - p * nv);
-    H[p * ldHp + colofs + k] = a[p * lda + k] + b[p * lda + k];
-  }
-}
-
 // start of a cycle for every problem: g = beta e_1, active while beta > target
 __global__ void k_seg_cycle_init(int32_t P, double* __restrict__ g, int32_t ldg, const double* __restrict__ beta,
                                  const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kcols,
@@ -128,11 +126,13 @@ __global__ void k_seg_cycle_init(int32_t P, double* __restrict__ g, int32_t ldg,
   if (threadIdx.x == 0) *any = s_any;
 }
 
-// Givens update of column j of every active problem's Hessenberg: apply the
+// Givens update of column j of every active problem's Hessenberg (formed here
+// as the sum of the two Gram-Schmidt passes; H[j+1][j] is already in place): apply the
 // previous rotations, form the one that zeroes H[j+1][j], rotate g; |g[j+1]|
 // is that problem's GMRES residual. A problem stops at its target or when its
 // Krylov space is exhausted (H[j+1][j] = 0). *any = some problem still active.
-__global__ void k_seg_givens(int32_t P, double* __restrict__ H, int32_t ldh, int32_t m, int32_t j,
+__global__ void k_seg_givens(int32_t P, const double* __restrict__ ha, const double* __restrict__ hb, int32_t lda,
+                             double* __restrict__ H, int32_t ldh, int32_t m, int32_t j,
                              double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
                              double* __restrict__ res, const double* __restrict__ target, int* __restrict__ active,
                              int* __restrict__ kcols, int* __restrict__ any) {
@@ -142,6 +142,7 @@ __global__ void k_seg_givens(int32_t P, double* __restrict__ H, int32_t ldh, int
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     if (active[p]) {
       double* h = H + (int64_t)p * ldh * m + (int64_t)j * ldh;
+      for (int i = 0; i <= j; ++i) h[i] = ha[(int64_t)p * lda + i] + hb[(int64_t)p * lda + i];
       double* c_ = cs + (int64_t)p * m;
       double* s_ = sn + (int64_t)p * m;
       double* gp = g + (int64_t)p * ldh;
@@ -245,15 +246,13 @@ inline int grid_for(int64_t work, int block) {
 void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
                      double* out, int32_t ldo, const int* guard, cudaStream_t s) {
   dim3 grid((unsigned)sg.n_chunks, (nv + MD - 1) / MD);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, nv, V, ldv, w, partial, nv, guard);
-  k_seg_reduce<<<sg.P, 256, 0, s>>>(sg, nv, partial, nv, out, ldo, 0, guard);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, nv, V, ldv, w, partial, out, ldo, 0, guard);
 }
 
 void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
                      const int* guard, cudaStream_t s) {
   dim3 grid((unsigned)sg.n_chunks, 1);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, 1, guard);
-  k_seg_reduce<<<sg.P, 32, 0, s>>>(sg, 1, partial, 1, out, ldo, 1, guard);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, out, ldo, 1, guard);
 }
 
 void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,
@@ -266,19 +265,15 @@ void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const do
   k_seg_scale_inv<<<grid_for(n, 256), 256, 0, s>>>(sg, n, x, scal, lds, y, guard);
 }
 
-void launch_seg_add(int32_t P, int32_t nv, const double* a, const double* b, int32_t lda, double* H, int32_t ldHp,
-                    int64_t colofs, const int* guard, cudaStream_t s) {
-  k_seg_add<<<grid_for((int64_t)P * nv, 128), 128, 0, s>>>(P, nv, a, b, lda, H, ldHp, colofs, guard);
-}
-
 void launch_seg_cycle_init(int32_t P, double* g, int32_t ldg, const double* beta, const double* target, int* active,
                            int* kcols, int* any, cudaStream_t s) {
   k_seg_cycle_init<<<1, 256, 0, s>>>(P, g, ldg, beta, target, active, kcols, any);
 }
 
-void launch_seg_givens(int32_t P, double* H, int32_t ldh, int32_t m, int32_t j, double* cs, double* sn, double* g,
-                       double* res, const double* target, int* active, int* kcols, int* any, cudaStream_t s) {
-  k_seg_givens<<<1, 256, 0, s>>>(P, H, ldh, m, j, cs, sn, g, res, target, active, kcols, any);
+void launch_seg_givens(int32_t P, const double* a, const double* b, int32_t lda, double* H, int32_t ldh, int32_t m,
+                       int32_t j, double* cs, double* sn, double* g, double* res, const double* target, int* active,
+                       int* kcols, int* any, cudaStream_t s) {
+  k_seg_givens<<<1, 256, 0, s>>>(P, a, b, lda, H, ldh, m, j, cs, sn, g, res, target, active, kcols, any);
 }
 
 void launch_seg_lsq(int32_t P, const double* H, int32_t ldh, int32_t m, const int* kcols, const double* g, double* y,
