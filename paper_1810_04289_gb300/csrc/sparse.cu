@@ -43,13 +43,23 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __re
     TX acc = TX(0);
     if (r < 7 && row < n) {
       const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
-      for (int64_t b = b0 + q; b < b1; b += S) {
-        const TV* A = vals + 49 * b + 7 * r;
-        const TX* xb = x + 7 * (int64_t)col[b];
-        TX s0 = TX(A[0]) * xb[0] + TX(A[1]) * xb[1];
-        TX s1 = TX(A[2]) * xb[2] + TX(A[3]) * xb[3];
-        TX s2 = TX(A[4]) * xb[4] + TX(A[5]) * xb[5];
-        acc += (s0 + s1) + (s2 + TX(A[6]) * xb[6]);
+      // four of this lane's blocks per pass: their column indices first, then
+      // all their loads, so that the loads of a pass are in flight together
+      for (int64_t b = b0 + q; b < b1; b += 4 * S) {
+        int cl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cl[u] = b + u * S < b1 ? col[b + u * S] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (cl[u] >= 0) {
+            const TV* A = vals + 49 * (b + u * S) + 7 * r;
+            const TX* xb = x + 7 * (int64_t)cl[u];
+            TX s0 = TX(A[0]) * xb[0] + TX(A[1]) * xb[1];
+            TX s1 = TX(A[2]) * xb[2] + TX(A[3]) * xb[3];
+            TX s2 = TX(A[4]) * xb[4] + TX(A[5]) * xb[5];
+            acc += (s0 + s1) + (s2 + TX(A[6]) * xb[6]);
+          }
+        }
       }
     }
 #pragma unroll
