@@ -181,7 +181,7 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     m = make_mesh(args.workload)
-    y0 = initial_state(m, fsi.fsi_default_options(precision=1, n_subdomains=args.subdomains))
+    y0 = initial_state(m, fsi.fsi_default_options(precision=1, n_subdomains=args.subdomains, ilu_level=args.ilu))
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
