@@ -39,6 +39,7 @@ WORKLOADS = {
 MATERIAL = dict(rho_f=1.05, mu_f=0.035, rho_s=1.2, E_s=3.0e6, nu_s=0.45, eta_s=0.0)
 S_F64 = 8
 S_F32 = 4
+METRIC = "FSI time steps/s on 1 GB300, mixed-precision vs FP64 at Newton rtol 1e-6"
 # DRAM bytes per launch (read + write) from one ncu capture of the kernel as it is
 # now, keyed by (workload, phase, precision, subdomains, ILU level, ordering);
 # the summary that holds the capture is named beside it
@@ -338,6 +339,7 @@ def cpu_sample(args, steps_hint=None):
     ni, nf = (steps_hint or (3.0, 4.0))
     t_step = ni * tJ + nf * tF
     return {"value": 1.0 / t_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "nodes": int(m.n_nodes), "tets": int(m.n_tets), "unknowns": int(vm.count_unknowns(m)),
             "sample": (f"{args.workload}: one residual ({tF:.2f} s) + complex-step Jacobian of 5% of the tets "
                        f"scaled to all ({tJ:.1f} s), per step {ni:.1f} Jacobians + {nf:.1f} residuals; "
                        f"direct solve not run (assembly-only, an upper bound on the oracle's steps/s)")}
@@ -360,10 +362,12 @@ def main():
                 vals.append(r["value"])
         v = float(np.mean(vals))
         cb = dict(r, value=v)
-        print(json.dumps({"impl": "reference", "metric": "FSI time steps/s on 1 GB300 (oracle on host cores)",
+        cfg = {"workload": args.workload, "nodes": cb.pop("nodes"), "unknowns": cb.pop("unknowns"),
+               "tets": cb.pop("tets"), "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol}
+        print(json.dumps({"impl": "reference", "metric": METRIC,
                           "value": v, "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps,
                           "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": args.workload},
+                          "data": "synthetic", "config": cfg,
                           "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
@@ -393,7 +397,7 @@ def main():
         except Exception as e:  # the baseline is context, never a reason to lose the GPU line
             cpu = {"value": None, "error": str(e)}
     line = {
-        "metric": "FSI time steps/s on 1 GB300, mixed-precision vs FP64 at Newton rtol 1e-6",
+        "metric": METRIC,
         "value": head["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if "mixed" in res else "f64", "data": "synthetic",
