@@ -175,6 +175,16 @@ def phase_model(info, s):
     }
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest replica's time: every rank gets the maximum of the ranks' ms."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1810_04289_gb300 import fsi
@@ -222,10 +232,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, "cuda")
         # e2e: through the public API with host buffers, per step H2D of the step's
         # inputs (y_n, y_{n-1}, y_{n-2}) from pinned memory and D2H of the result
         e2e = None

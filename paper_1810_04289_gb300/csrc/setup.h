@@ -1,5 +1,5 @@
 // Host-side symbolic setup of the solver: block-sparse pattern, assembly gather
-// lists, Schwarz subdomains (partition, overlap, RCM order), ILU(0) update lists
+// lists, Schwarz subdomains (partition, overlap, RCM order), ILU(k) update lists
 // and level schedules. Everything here runs once per mesh in fsi_create.
 #pragma once
 #include <cstdint>

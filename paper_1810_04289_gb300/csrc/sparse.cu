@@ -1,9 +1,9 @@
 // Block-sparse (7x7 BSR) matrix-vector product and the restricted additive
-// Schwarz preconditioner of Sec. 3, Eq. 14-16, with block ILU(0) subdomain
-// solves: extraction of the overlapped submatrices J_i^delta, batched
-// level-scheduled factorisation (one CTA per subdomain), and the
+// Schwarz preconditioner of Sec. 3, Eq. 14-16, with block ILU(k) subdomain
+// solves: extraction of the overlapped submatrices J_i^delta, the batched
+// factorisation (one CTA per subdomain, all subdomains in one launch), and the
 // level-scheduled forward/backward solves with the restricted (owned-rows-only)
-// prolongation.
+// prolongation used when the TMA-fed apply (ras_stream.cu) does not fit.
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
