@@ -167,6 +167,7 @@ typedef struct {
   int64_t factor_rows;         /* block rows of all overlapped subdomains */
   int32_t max_levels;          /* deepest level schedule over the subdomains */
   int64_t device_bytes;        /* device memory held by the context */
+  int64_t n_wss_faces;         /* inner-wall faces (fluid tet against wall tet) */
 } fsi_info;
 
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,
@@ -235,6 +236,23 @@ fsi_status fsi_linear_solve(fsi_ctx *ctx, const double *rhs, double *x, fsi_solv
  * then shift the time levels (y_{n-2} <- y_{n-1} <- y_n <- y, t <- t + dt). On
  * failure the state is left at the previous time level. stats may be NULL. */
 fsi_status fsi_step(fsi_ctx *ctx, fsi_step_stats *stats);
+
+/* Wall shear stress on the inner wall of every problem (the WSS and SAWSS
+ * formulas of the paper's results section, with sigma_f of Eq. 3): on each face
+ * shared by a fluid tet and a wall tet, WSS = sigma n - (sigma n . n) n with
+ * sigma = -p I + 2 mu_f eps(u) of the P1 fluid tet on the current configuration
+ * x = X + d, p at the face centroid and n the unit normal out of the fluid;
+ * SAWSS of a problem = sum of |WSS| x face area / sum of face areas.
+ * y: device [n_nodes*7] FP64 state. wss: device [n_wss_faces*3] FP64 output, or
+ * NULL. sawss: host [n_problems] output, or NULL (when given, the call waits for
+ * the stream). Faces are ordered as fsi_wss_faces lists them. */
+fsi_status fsi_wss(fsi_ctx *ctx, const double *y, double *wss, double *sawss);
+
+/* The inner-wall faces used by fsi_wss, in its order (by problem, then fluid
+ * tet in input order, then face): n_faces gets their count; tet_face (host
+ * [n_faces*2], may be NULL) gets, per face, the input index of its fluid tet and
+ * the local index (0..3) of that tet's vertex opposite the face. */
+fsi_status fsi_wss_faces(const fsi_ctx *ctx, int64_t *n_faces, int32_t *tet_face);
 
 fsi_status fsi_get_info(const fsi_ctx *ctx, fsi_info *info);
 

@@ -424,3 +424,78 @@ def run_steps(prob, y0, n_steps, t0=0.0, **kw):
         out.append((y, hist))
         y2, y1 = y1, y
     return out
+
+
+# ----------------------------------------------------------------------------
+# wall shear stress (Sec. 4, results: the WSS and SAWSS formulas)
+# ----------------------------------------------------------------------------
+def wss_faces(tets, tet_domain, node_problem):
+    """The inner wall surface: faces shared by a fluid tet and a wall tet.
+
+    Faces are matched by their sorted vertex triple (a plain dictionary, one pass
+    over all faces). Returns an (F, 2) int64 array of (fluid tet, local index of
+    the vertex opposite the face), sorted by (problem of the tet's first vertex,
+    tet, local index).
+    """
+    tets = np.asarray(tets)
+    owners = {}
+    for t in range(tets.shape[0]):
+        for f in range(4):
+            key = tuple(sorted(int(tets[t, a]) for a in range(4) if a != f))
+            owners.setdefault(key, []).append((t, f))
+    out = []
+    for lst in owners.values():
+        if len(lst) != 2:
+            continue
+        (t0, f0), (t1, f1) = lst
+        if tet_domain[t0] == 0 and tet_domain[t1] == 1:
+            out.append((t0, f0))
+        elif tet_domain[t1] == 0 and tet_domain[t0] == 1:
+            out.append((t1, f1))
+    prob = np.asarray(node_problem)
+    out.sort(key=lambda tf: (int(prob[tets[tf[0], 0]]), tf[0], tf[1]))
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def wall_shear_stress(X, tets, tet_domain, node_problem, y, mu, n_problems=1):
+    """Per-face WSS vectors and the spatially averaged WSS of every problem.
+
+    On each inner-wall face, with the fluid stress sigma = -p I + 2 mu eps(u)
+    (Eq. 3) of the adjacent fluid tet on the current configuration x = X + d
+    (P1: eps constant on the tet, p taken at the face centroid) and n the unit
+    normal pointing out of the fluid:
+        WSS = sigma n - (sigma n . n) n,
+    and SAWSS = (1/A) sum over faces of |WSS| area, A = total face area (the
+    surface integral of the WSS magnitude over the inner wall, normalised by its
+    area). Returns (faces (F,2), wss (F,3), area (F,), sawss (n_problems,)).
+    """
+    faces = wss_faces(tets, tet_domain, node_problem)
+    y = np.asarray(y, dtype=np.float64)
+    F = faces.shape[0]
+    wss = np.zeros((F, 3))
+    area = np.zeros(F)
+    num = np.zeros(n_problems)
+    den = np.zeros(n_problems)
+    for i, (t, f) in enumerate(faces):
+        v = np.asarray(tets[t], dtype=np.int64)
+        x = X[v] + y[v, 4:7]
+        g, _ = p1_gradients(x[None])
+        G = y[v, 0:3].T @ g[0]                      # (grad u)_ij = sum_a u_a,i dN_a/dx_j
+        eps = 0.5 * (G + G.T)
+        fv = [a for a in range(4) if a != f]
+        xa, xb, xc = x[fv[0]], x[fv[1]], x[fv[2]]
+        cr = np.cross(xb - xa, xc - xa)
+        A = 0.5 * np.linalg.norm(cr)
+        n = cr / np.linalg.norm(cr)
+        if np.dot(n, (xa + xb + xc) / 3.0 - x[f]) < 0:
+            n = -n                                  # out of the fluid tet
+        p = np.mean(y[v[fv], 3])
+        sn = -p * n + 2.0 * mu * (eps @ n)
+        w = sn - np.dot(sn, n) * n
+        wss[i] = w
+        area[i] = A
+        q = int(node_problem[v[0]])
+        num[q] += np.linalg.norm(w) * A
+        den[q] += A
+    sawss = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    return faces, wss, area, sawss

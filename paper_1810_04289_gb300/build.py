@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libfsi_gb300.so")
-SOURCES = ["setup.cpp", "assembly.cu", "sparse.cu", "ras_stream.cu", "krylov.cu", "api.cu"]
+SOURCES = ["setup.cpp", "assembly.cu", "sparse.cu", "ras_stream.cu", "krylov.cu", "wss.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

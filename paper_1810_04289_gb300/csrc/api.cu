@@ -83,6 +83,13 @@ struct fsi_ctx {
   double *V = nullptr, *Z = nullptr, *r = nullptr;
   double *H = nullptr, *g = nullptr, *cs = nullptr, *sn = nullptr, *ylsq = nullptr, *hA = nullptr, *hB = nullptr;
   double* partial = nullptr;     // [chunks][m+1] reduction partials
+  // inner-wall faces for the wall shear stress
+  int64_t nwss = 0;
+  int64_t* wface = nullptr;              // [nwss] 4 * internal fluid tet + opposite vertex
+  int64_t* wfb = nullptr;                // [P+1] face offsets of the problems
+  double *wma = nullptr, *wa = nullptr;  // [nwss] |WSS| area and area
+  double* wsawss = nullptr;              // [P]
+  std::vector<int32_t> wface_host;       // [nwss*2] input tet, opposite vertex
   double* beta = nullptr;        // [P] norms (residual of the cycle, Newton norms)
   double* gres = nullptr;        // [P] Givens residual estimates
   double* gtarget = nullptr;     // [P] GMRES stopping thresholds
@@ -535,14 +542,16 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
 
     const int64_t N = mesh->n_nodes, T0 = mesh->n_tets;
     // validate, then order tets fluid first
-    std::vector<int32_t> tets;
+    std::vector<int32_t> tets, tet_src;
     tets.reserve(4 * T0);
+    tet_src.reserve(T0);
     int64_t Tf = 0;
     for (int pass = 0; pass < 2; ++pass)
       for (int64_t t = 0; t < T0; ++t) {
         const uint8_t d = mesh->tet_domain[t];
         if (d > 1) throw StatusError{FSI_ERR_MESH, "tet_domain must be 0 or 1"};
         if (d != pass) continue;
+        tet_src.push_back((int32_t)t);
         for (int a = 0; a < 4; ++a) {
           const int32_t v = mesh->tets[4 * t + a];
           if (v < 0 || v >= N) throw StatusError{FSI_ERR_MESH, "tet vertex index out of range"};
@@ -584,6 +593,46 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (wl && bc[p].rigid_wall) f |= NF_D_ZERO;
       if (!fl && !wl) f |= NF_U_IDENT | NF_P_IDENT | NF_D_ZERO;  // isolated node
       flag[i] = f;
+    }
+    // inner-wall faces (fluid tet against wall tet), matched by sorted vertex
+    // triples among the faces whose three vertices are interface nodes
+    std::vector<int64_t> wface;
+    std::vector<int64_t> wfb(n_problems + 1, 0);
+    {
+      struct FaceKey {
+        int32_t a, b, c;
+        int64_t tf;  // 4 * internal tet + opposite vertex
+      };
+      std::vector<FaceKey> cand;
+      for (int64_t t = 0; t < T0; ++t)
+        for (int f = 0; f < 4; ++f) {
+          int32_t v[3], k = 0;
+          for (int a = 0; a < 4; ++a)
+            if (a != f) v[k++] = tets[4 * t + a];
+          if (!(mesh->node_tag[v[0]] & mesh->node_tag[v[1]] & mesh->node_tag[v[2]] & FSI_TAG_INTERFACE)) continue;
+          std::sort(v, v + 3);
+          cand.push_back({v[0], v[1], v[2], 4 * t + f});
+        }
+      std::sort(cand.begin(), cand.end(), [](const FaceKey& x, const FaceKey& y) {
+        if (x.a != y.a) return x.a < y.a;
+        if (x.b != y.b) return x.b < y.b;
+        if (x.c != y.c) return x.c < y.c;
+        return x.tf < y.tf;
+      });
+      for (size_t i = 0; i + 1 < cand.size(); ++i) {
+        const FaceKey &x = cand[i], &y = cand[i + 1];
+        if (x.a != y.a || x.b != y.b || x.c != y.c) continue;
+        const bool fx = (x.tf >> 2) < Tf, fy = (y.tf >> 2) < Tf;
+        if (fx != fy) wface.push_back(fx ? x.tf : y.tf);
+        ++i;
+      }
+      auto pr = [&](int64_t tf) { return prob[tets[4 * (tf >> 2)]]; };
+      std::sort(wface.begin(), wface.end(), [&](int64_t x, int64_t y) {
+        const int32_t px = pr(x), py = pr(y);
+        return px != py ? px < py : x < y;
+      });
+      for (int64_t tf : wface) wfb[pr(tf) + 1]++;
+      for (int p = 0; p < n_problems; ++p) wfb[p + 1] += wfb[p];
     }
     std::vector<double> inl((size_t)INLET_STRIDE * n_problems);
     for (int p = 0; p < n_problems; ++p) {
@@ -650,6 +699,17 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->vals = cp->dalloc<char>((int64_t)(49 * vs) * cp->nnzb);
     CK(cudaMemsetAsync(cp->vals, 0, 49 * vs * cp->nnzb, cp->s));
     cp->mesh = MeshDev{N, T0, Tf, cp->X, cp->tets, cp->nflag, cp->nprobid, cp->inlet};
+    cp->nwss = (int64_t)wface.size();
+    cp->wface = cp->upload(wface);
+    cp->wfb = cp->upload(wfb);
+    cp->wma = cp->dalloc<double>(std::max<int64_t>(cp->nwss, 1));
+    cp->wa = cp->dalloc<double>(std::max<int64_t>(cp->nwss, 1));
+    cp->wsawss = cp->dalloc<double>(n_problems);
+    cp->wface_host.resize(2 * wface.size());
+    for (size_t i = 0; i < wface.size(); ++i) {
+      cp->wface_host[2 * i] = tet_src[wface[i] >> 2];
+      cp->wface_host[2 * i + 1] = (int32_t)(wface[i] & 3);
+    }
 
     const int64_t n = 7 * N;
     cp->yn = cp->dalloc<double>(n);
@@ -1117,6 +1177,28 @@ fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
   info->factor_rows = (int64_t)c->plan.gnode.size();
   info->max_levels = c->plan.max_levels;
   info->device_bytes = c->dev_bytes;
+  info->n_wss_faces = c->nwss;
+  return FSI_OK;
+}
+
+fsi_status fsi_wss(fsi_ctx* c, const double* y, double* wss, double* sawss) {
+  if (!c) return FSI_ERR_ARG;
+  return guarded(c, [&]() -> fsi_status {
+    if (!y) throw StatusError{FSI_ERR_ARG, "y is null"};
+    launch_wss(c->mesh, c->mat.mu_f, c->nwss, c->wface, c->wfb, c->nprob, y, wss, c->wma, c->wa, c->wsawss, c->s);
+    check_launch();
+    if (sawss) {
+      CK(cudaMemcpyAsync(sawss, c->wsawss, sizeof(double) * c->nprob, cudaMemcpyDeviceToHost, c->s));
+      CK(cudaStreamSynchronize(c->s));
+    }
+    return FSI_OK;
+  });
+}
+
+fsi_status fsi_wss_faces(const fsi_ctx* c, int64_t* n_faces, int32_t* tet_face) {
+  if (!c || !n_faces) return FSI_ERR_ARG;
+  *n_faces = c->nwss;
+  if (tet_face) std::memcpy(tet_face, c->wface_host.data(), sizeof(int32_t) * c->wface_host.size());
   return FSI_OK;
 }
 

@@ -20,6 +20,11 @@ struct MeshDev {
   const double* inlet;       // [nprob*INLET_STRIDE]
 };
 
+// ---- wall shear stress (wss.cu): face = 4 * fluid tet + local index of the
+// vertex opposite the face; fb = [P+1] face offsets of the problems
+void launch_wss(const MeshDev& m, double mu, int64_t nf, const int64_t* face, const int64_t* fb, int32_t P,
+                const double* y, double* wss, double* marea, double* area, double* sawss, cudaStream_t s);
+
 // ---- assembly (assembly.cu)
 void launch_elem_residual(const MeshDev& m, const MatConst& mc, const double* y, const double* y1,
                           const double* y2, double* Fe, cudaStream_t s);

@@ -22,7 +22,8 @@ STATUS = {0: "FSI_OK", 1: "FSI_ERR_ARG", 2: "FSI_ERR_MESH", 3: "FSI_ERR_CUDA", 4
 # every symbol include/fsi.h declares
 EXPORTS = ["fsi_default_options", "fsi_create", "fsi_destroy", "fsi_set_state", "fsi_get_state",
            "fsi_residual", "fsi_jacobian", "fsi_jacobian_export", "fsi_spmv", "fsi_pc_apply",
-           "fsi_linear_solve", "fsi_step", "fsi_get_info", "fsi_last_error", "fsi_residual_noalloc"]
+           "fsi_linear_solve", "fsi_step", "fsi_get_info", "fsi_last_error", "fsi_residual_noalloc",
+           "fsi_wss", "fsi_wss_faces"]
 
 
 class FsiMesh(ctypes.Structure):
@@ -71,7 +72,7 @@ class FsiInfo(ctypes.Structure):
                 ("nnzb", ctypes.c_int64), ("n_fluid_tets", ctypes.c_int64), ("n_wall_tets", ctypes.c_int64),
                 ("n_problems", ctypes.c_int32), ("n_subdomains", ctypes.c_int32),
                 ("factor_blocks", ctypes.c_int64), ("factor_rows", ctypes.c_int64), ("max_levels", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_wss_faces", ctypes.c_int64)]
 
 
 def load_library(path=LIB_PATH):
@@ -97,6 +98,8 @@ def load_library(path=LIB_PATH):
         "fsi_get_info": (ctypes.c_int, [P, ctypes.POINTER(FsiInfo)]),
         "fsi_last_error": (ctypes.c_char_p, [P]),
         "fsi_residual_noalloc": (ctypes.c_int, [P, P, P]),
+        "fsi_wss": (ctypes.c_int, [P, P, P, P]),
+        "fsi_wss_faces": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -242,6 +245,24 @@ def fsi_step(ctx, stats=True):
     return s
 
 
+def fsi_wss(ctx, y, wss=None):
+    """Wall shear stress: fills the device tensor wss ([n_wss_faces, 3] FP64, or
+    None) and returns the per-problem SAWSS as a numpy array."""
+    n = fsi_get_info(ctx).n_problems
+    out = np.zeros(n, dtype=np.float64)
+    _check(ctx, lib().fsi_wss(ctx, _dptr(y), _dptr(wss) if wss is not None else None, out.ctypes.data))
+    return out
+
+
+def fsi_wss_faces(ctx):
+    """(n_faces, (n_faces, 2) int32 array of input fluid tet and opposite vertex)."""
+    n = ctypes.c_int64()
+    _check(ctx, lib().fsi_wss_faces(ctx, ctypes.byref(n), None))
+    tf = np.zeros((n.value, 2), dtype=np.int32)
+    _check(ctx, lib().fsi_wss_faces(ctx, ctypes.byref(n), tf.ctypes.data))
+    return n.value, tf
+
+
 def fsi_get_info(ctx):
     i = FsiInfo()
     _check(ctx, lib().fsi_get_info(ctx, ctypes.byref(i)))
@@ -322,3 +343,10 @@ class Solver:
 
     def step(self):
         return fsi_step(self.ctx)
+
+    def wss(self, y):
+        """(faces (F,2), WSS vectors (F,3), SAWSS per problem) for the state y."""
+        n, faces = fsi_wss_faces(self.ctx)
+        w = self.torch.zeros((max(n, 1), 3), dtype=self.torch.float64, device="cuda")
+        sawss = fsi_wss(self.ctx, self.vec(y), w)
+        return faces, w[:n].cpu().numpy(), sawss

@@ -517,3 +517,44 @@ def test_newton_step_quadratic_and_volume_balance():
     q_in = -cap_flux(y2, vm.INLET)
     assert abs(dV) > 1e-4 * q_in          # the wall does move
     assert abs(q_net - dV) < 1e-6 * q_in, (q_net, dV, q_in)
+
+
+# ---------------------------------------------------------------------------
+# wall shear stress (results section: WSS = sigma n - (sigma n . n) n, SAWSS)
+# ---------------------------------------------------------------------------
+def test_wss_poiseuille_converges_to_closed_form():
+    """Rigid-tube Poiseuille u = U (1 - r^2/R^2) e_z: the wall shear stress is
+    mu |du/dr| at r = R = 2 mu U / R = 4.2 dyn/cm^2 (textbook). The P1 gradient in
+    the wall-adjacent tets is a secant slope, so SAWSS converges at first order.
+    The inner wall of the polygonal tube has area L n_theta 2R sin(pi/n_theta)
+    exactly, and the traction the wall puts on the fluid opposes the flow (-z),
+    which fixes the orientation of n."""
+    mu, U, R, L = 0.035, 30.0, 0.5, 4.0
+    exact = 2.0 * mu * U / R
+    errs = []
+    for nz, nt, nrf, nrw in ((12, 8, 3, 1), (24, 16, 6, 2), (48, 32, 12, 4)):
+        m = vm.tube_mesh(nz, nt, nrf, nrw, jitter=0.0)
+        y = vm.poiseuille_state(m)
+        _, w, a, s = O.wall_shear_stress(m.X, m.tets, m.tet_domain, m.node_problem, y, mu)
+        assert abs(a.sum() - L * nt * 2 * R * np.sin(np.pi / nt)) < 1e-12 * a.sum()
+        assert (w[:, 2] < 0).all()
+        errs.append(abs(s[0] - exact))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] / errs[2] > 1.5 and errs[2] < 0.05 * exact
+
+
+def test_wss_ignores_pressure_and_rigid_rotation():
+    """The tangential projection removes -p n whatever p is, and a rigid rotation
+    u = omega x X has eps(u) = 0, so its WSS vanishes (a transposed or unsymmetrised
+    velocity gradient would not)."""
+    m = vm.tube_config("tube-12x8x4")
+    y = vm.poiseuille_state(m)
+    _, w, _, _ = O.wall_shear_stress(m.X, m.tets, m.tet_domain, m.node_problem, y, 0.035)
+    y2 = y.copy()
+    y2[:, 3] += 100.0 + 3.0 * m.X[:, 0] - 7.0 * m.X[:, 2]
+    _, w2, _, _ = O.wall_shear_stress(m.X, m.tets, m.tet_domain, m.node_problem, y2, 0.035)
+    assert np.abs(w2 - w).max() < 1e-12 * np.abs(w).max() * 100
+    y3 = np.zeros_like(y)
+    y3[:, 0:3] = np.cross(np.array([0.3, -1.2, 0.7]), m.X)
+    _, w3, _, _ = O.wall_shear_stress(m.X, m.tets, m.tet_domain, m.node_problem, y3, 0.035)
+    assert np.abs(w3).max() < 1e-13
