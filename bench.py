@@ -206,12 +206,13 @@ def run_ours(args, rank, world):
                                       precision=pflag)
         tuned = None
         if not args.no_autotune:
-            from paper_1810_04289_gb300.autotune import autotune
+            from paper_1810_04289_gb300.autotune import autotune, tune_jac_lag
             t_tune = time.perf_counter()
             opt, table = autotune(m, MATERIAL, y0, base=opt)
+            opt, lag_table = tune_jac_lag(m, MATERIAL, y0, opt)
             tuned = {"chosen": {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level", "ordering",
-                                                             "threads_per_row")},
-                     "seconds": time.perf_counter() - t_tune, "candidates": table}
+                                                             "threads_per_row", "jac_lag")},
+                     "seconds": time.perf_counter() - t_tune, "candidates": table, "jac_lag": lag_table}
         S = fsi.Solver(m, MATERIAL, opt)
         info = S.info()
         S.set_state(y0, t=0.0)
@@ -414,6 +415,7 @@ def main():
                    "overlap": (head["tuned"] or {}).get("chosen", {}).get("overlap", args.overlap),
                    "ilu": (head["tuned"] or {}).get("chosen", {}).get("ilu_level", args.ilu),
                    "ordering": (head["tuned"] or {}).get("chosen", {}).get("ordering", 1),
+                   "jac_lag": (head["tuned"] or {}).get("chosen", {}).get("jac_lag", 1),
                    "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol,
                    "l2": "working set (BSR + ILU factors) larger than L2 each step",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -5,7 +5,9 @@ ABI, one Newton linear system per candidate: preconditioner setup (extraction,
 ILU factorisation, packing) plus the GMRES solve to the candidate's tolerance.
 Candidates vary the Schwarz subdomain count, the overlap, the ILU fill level and
 the SpMV threads per block row (default grid: see default_grid); the fastest
-converged time to solution wins. The solver
+converged time to solution wins. tune_jac_lag then picks the Jacobian lag (how
+many Newton iterations reuse one Jacobian and its factors, Eq. 12 and the
+paper's Table 3) by timing whole time steps. The solver
 arithmetic itself is unchanged by any choice (only the preconditioner and the
 launch mapping change), so the tuned options solve the same equations.
 """
@@ -82,4 +84,45 @@ def autotune(mesh, material, y0, base=None, grid=None, t0=0.0, verbose=False):
             best = (secs, opt)
     if best is None:
         raise RuntimeError(f"no candidate converged: {results}")
+    return best[1], results
+
+
+def tune_jac_lag(mesh, material, y0, base, lags=(1, 2, 3), steps=2, t0=0.0, verbose=False):
+    """Return (best FsiOptions, list of result dicts): for each Jacobian lag, one
+    untimed time step from y0, then `steps` timed steps; the fastest run whose
+    steps all converged wins. The Newton tolerance is the same for every lag, so
+    each run solves the same steps to the same accuracy."""
+    import torch
+    results = []
+    best = None
+    for lag in lags:
+        opt = fsi.FsiOptions()
+        for f, _ in fsi.FsiOptions._fields_:
+            setattr(opt, f, getattr(base, f))
+        opt.jac_lag = lag
+        S = fsi.Solver(mesh, material, opt)
+        S.set_state(y0, t=t0)
+        try:
+            S.step()
+            torch.cuda.synchronize()
+            tic = time.perf_counter()
+            its = []
+            for _ in range(steps):
+                st = S.step()
+                its.append((st.newton_iterations, st.linear_iterations))
+            torch.cuda.synchronize()
+            secs = (time.perf_counter() - tic) / steps
+        except fsi.FsiError as e:
+            results.append(dict(jac_lag=lag, error=str(e)))
+            S.close()
+            continue
+        S.close()
+        rec = dict(jac_lag=lag, seconds_per_step=secs, newton_linear_iterations=its)
+        results.append(rec)
+        if verbose:
+            print("jac_lag", rec, flush=True)
+        if best is None or secs < best[0]:
+            best = (secs, opt)
+    if best is None:
+        raise RuntimeError(f"no Jacobian lag ran: {results}")
     return best[1], results

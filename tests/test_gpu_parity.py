@@ -218,3 +218,19 @@ def test_factor_shared_memory_modes_are_bitwise_identical(tube0, precision, ilu)
         S.close()
     assert np.isfinite(outs[0]).all()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_newton_steps_with_jacobian_lag_match_oracle(tube0, oracle_tube0_steps):
+    """Reusing one Jacobian and its factors for three Newton iterations (Eq. 12,
+    the paper's Jacobian lag) changes the path, not the solution: the steps still
+    match the oracle's exact-Newton steps to 1e-8."""
+    y0, ref = oracle_tube0_steps
+    S = make_solver(tube0, newton_rtol=1e-10, gmres_rtol=1e-6, n_subdomains=4, jac_lag=3)
+    S.set_state(y0, t=0.0)
+    for k in range(5):
+        st = S.step()
+        y, _ = S.state()
+        rel = rel_by_group(y, ref[k])
+        assert st.converged == 1
+        assert st.jacobian_evaluations <= -(-st.newton_iterations // 3)
+        assert all(v < 1e-8 for v in rel.values()), (k, rel)
