@@ -72,7 +72,9 @@ enum {
  *   tet_domain   [n_tets]     0 = fluid (lumen), 1 = wall
  *   node_tag     [n_nodes]    FSI_TAG_* bits
  *   node_problem [n_nodes]    problem id of each node for batched meshes of
- *                             independent vessels, or NULL for one problem */
+ *                             independent vessels (non-decreasing: each
+ *                             problem's nodes stored one after another;
+ *                             otherwise FSI_ERR_MESH), or NULL for one problem */
 typedef struct {
   int64_t n_nodes, n_tets;
   const double *X;
