@@ -88,3 +88,15 @@ def test_create_rejects_bad_meshes_and_options_on_the_host():
     m, keep = _mesh_struct(X, T, D, G)
     st, ctx = _create(m, fsi.fsi_default_options(precision=5))
     assert st == 1 and not ctx.value
+
+
+def test_autotune_default_grid():
+    """Subdomain counts are powers of two giving 40..1000 nodes per subdomain;
+    both ILU levels and both RCM orders are searched, overlap 1, one warp per row."""
+    from paper_1810_04289_gb300.autotune import default_grid
+    g = default_grid(46657)
+    assert g["n_subdomains"] == (64, 128, 256, 512, 1024)
+    assert all(40 <= 46657 / k <= 1000 for k in g["n_subdomains"])
+    assert g["ilu_level"] == (1, 2) and g["ordering"] == (1, 2)
+    assert g["overlap"] == (1,) and g["threads_per_row"] == (32,)
+    assert default_grid(30)["n_subdomains"] == (1,)
