@@ -88,6 +88,18 @@ def test_create_rejects_bad_meshes_and_options_on_the_host():
     m, keep = _mesh_struct(X, T, D, G)
     st, ctx = _create(m, fsi.fsi_default_options(precision=5))
     assert st == 1 and not ctx.value
+    # empty inputs and out-of-range options are refused before any device work
+    m, keep = _mesh_struct(X, T[:0], D[:0], G)
+    assert _create(m, fsi.fsi_default_options())[0] == 1            # no tets
+    m, keep = _mesh_struct(X[:0], T[:0], D[:0], G[:0])
+    assert _create(m, fsi.fsi_default_options())[0] == 1            # no nodes
+    bad_d = D.copy()
+    bad_d[0] = 3
+    m, keep = _mesh_struct(X, T, bad_d, G)
+    assert _create(m, fsi.fsi_default_options())[0] == 2            # domain not 0/1
+    m, keep = _mesh_struct(X, T, D, G)
+    assert _create(m, fsi.fsi_default_options(gmres_restart=65))[0] == 1
+    assert _create(m, fsi.fsi_default_options(ilu_level=4))[0] == 1
 
 
 def test_autotune_default_grid():
