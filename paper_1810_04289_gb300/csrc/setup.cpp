@@ -2,7 +2,6 @@
 #include "setup.h"
 
 #include <algorithm>
-#include <map>
 #include <cmath>
 #include <numeric>
 #include <stdexcept>
@@ -146,6 +145,11 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
 #pragma omp parallel
   {
   std::vector<int32_t> loc(n, -1), mark(n, -1);
+  // symbolic ILU(k) row in a sorted linked list over local columns (END = none),
+  // with the level and the extraction source of each entry, and a dense map
+  // from column to position for the update lists
+  std::vector<int32_t> nxt(n + 1, -1), lev(n + 1, 0);
+  std::vector<int64_t> src(n + 1, -1), posq(n + 1, -1);
 #pragma omp for schedule(dynamic, 1)
   for (int32_t s = 0; s < np; ++s) {
     RasPlan& R = subs[s];
@@ -249,36 +253,56 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
     std::vector<std::vector<int32_t>> rcol(m);
     std::vector<std::vector<int32_t>> rlev(m);
     std::vector<std::vector<int64_t>> rgb(m);
-    std::map<int32_t, std::pair<int32_t, int64_t>> row;
+    const int32_t END = (int32_t)m;  // list terminator, larger than every column
+    std::vector<std::pair<int32_t, int64_t>> orig;
     for (int64_t q = 0; q < m; ++q) {
       int32_t v = gn[q];
       R.gnode.push_back(v);
       R.owned.push_back(owner[v] == s ? 1 : 0);
-      row.clear();
+      // the row of J_i^delta (level 0), sorted by local column
+      orig.clear();
       for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
         int32_t w = loc[P.col[e]];
-        if (w >= 0) row[w] = {0, e};
+        if (w >= 0) orig.push_back({w, e});
       }
+      std::sort(orig.begin(), orig.end());
+      int32_t head = END;
+      for (size_t k = orig.size(); k-- > 0;) {
+        const int32_t w = orig[k].first;
+        nxt[w] = head;
+        lev[w] = 0;
+        src[w] = orig[k].second;
+        head = w;
+      }
+      // level-of-fill: walk the L part in increasing column order (entries
+      // created on the way are visited too) and merge each row k's U part,
+      // level(q,j) = min over k of level(q,k) + level(k,j) + 1, kept if <= k_fill
       if (fill_level > 0) {
-        for (auto it = row.begin(); it != row.end() && it->first < q; ++it) {
-          const int32_t k = it->first;
-          const int32_t lqk = it->second.first;
+        for (int32_t k = head; k != END && k < q; k = nxt[k]) {
+          const int32_t lqk = lev[k];
+          int32_t prev = k;
           for (size_t f = 0; f < rcol[k].size(); ++f) {
             const int32_t j = rcol[k][f];
             if (j <= k) continue;
             const int32_t nl = lqk + rlev[k][f] + 1;
             if (nl > fill_level) continue;
-            auto jt = row.find(j);
-            if (jt == row.end()) row[j] = {nl, -1};
-            else if (nl < jt->second.first) jt->second.first = nl;
+            while (nxt[prev] < j) prev = nxt[prev];
+            if (nxt[prev] == j) {
+              if (nl < lev[j]) lev[j] = nl;
+            } else {
+              nxt[j] = nxt[prev];
+              nxt[prev] = j;
+              lev[j] = nl;
+              src[j] = -1;
+            }
+            prev = j;
           }
         }
       }
-      rcol[q].reserve(row.size());
-      for (auto& kv : row) {
-        rcol[q].push_back(kv.first);
-        rlev[q].push_back(kv.second.first);
-        rgb[q].push_back(kv.second.second);
+      for (int32_t k = head; k != END; k = nxt[k]) {
+        rcol[q].push_back(k);
+        rlev[q].push_back(lev[k]);
+        rgb[q].push_back(src[k]);
       }
     }
     for (int64_t q = 0; q < m; ++q) {
@@ -294,26 +318,28 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
     int32_t nlevL = 0, nlevU = 0;
     for (int64_t q = 0; q < m; ++q) {
       const int64_t rb = R.row_ptr[r0 + q], re = R.row_ptr[r0 + q + 1];
+      for (int64_t e = rb; e < re; ++e) posq[R.col[e] - r0] = e;
       for (int64_t e = rb; e < re; ++e) {
         const int64_t k = R.col[e] - r0;
         if (k >= q) break;
         levL[q] = std::max(levL[q], levL[k] + 1);
         R.lent_pos.push_back(e);
         R.lent_kdiag.push_back(R.diag[r0 + k]);
-        // updates A_qj -= A_qk A_kj for j > k in row k with (q, j) in the pattern
+        // updates A_qj -= A_qk A_kj for j > k in row k with (q, j) in the pattern,
+        // in row k's column order
         const int64_t kb = R.row_ptr[r0 + k], ke = R.row_ptr[r0 + k + 1];
-        int64_t pq = e + 1;
         for (int64_t f = kb; f < ke; ++f) {
           const int64_t j = R.col[f] - r0;
           if (j <= k) continue;
-          while (pq < re && R.col[pq] - r0 < j) ++pq;
-          if (pq < re && R.col[pq] - r0 == j) {
+          const int64_t pq = posq[j];
+          if (pq >= 0) {
             R.upd_tgt.push_back(pq);
             R.upd_src.push_back(f);
           }
         }
         R.upd_ptr.push_back((int64_t)R.upd_tgt.size());
       }
+      for (int64_t e = rb; e < re; ++e) posq[R.col[e] - r0] = -1;
       R.lent_ptr.push_back((int64_t)R.lent_pos.size());
       nlevL = std::max(nlevL, levL[q] + 1);
     }
@@ -347,34 +373,71 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
   }  // omp parallel
 
   // concatenate: rows, blocks, L entries, updates and levels get the offsets of
-  // the subdomains before them
-  init_plan(R);
+  // the subdomains before them (sizes and offsets first, then the copies in
+  // parallel, one subdomain per task)
+  std::vector<int64_t> oR(np + 1, 0), oB(np + 1, 0), oL(np + 1, 0), oU(np + 1, 0);
+  std::vector<int64_t> oLR(np + 1, 0), oUR(np + 1, 0), oLP(np + 1, 0), oUP(np + 1, 0);
   for (int32_t s = 0; s < np; ++s) {
-    RasPlan& L = subs[s];
-    const int64_t RO = (int64_t)R.gnode.size(), BO = (int64_t)R.col.size();
-    const int64_t LO = (int64_t)R.lent_pos.size(), UO = (int64_t)R.upd_tgt.size();
-    R.gnode.insert(R.gnode.end(), L.gnode.begin(), L.gnode.end());
-    R.owned.insert(R.owned.end(), L.owned.begin(), L.owned.end());
-    for (size_t i = 1; i < L.row_ptr.size(); ++i) R.row_ptr.push_back(L.row_ptr[i] + BO);
-    for (int32_t c : L.col) R.col.push_back((int32_t)(c + RO));
-    R.gblk.insert(R.gblk.end(), L.gblk.begin(), L.gblk.end());
-    for (int64_t d : L.diag) R.diag.push_back(d + BO);
-    for (size_t i = 1; i < L.lent_ptr.size(); ++i) R.lent_ptr.push_back(L.lent_ptr[i] + LO);
-    for (int64_t v : L.lent_pos) R.lent_pos.push_back(v + BO);
-    for (int64_t v : L.lent_kdiag) R.lent_kdiag.push_back(v + BO);
-    for (size_t i = 1; i < L.upd_ptr.size(); ++i) R.upd_ptr.push_back(L.upd_ptr[i] + UO);
-    for (int64_t v : L.upd_tgt) R.upd_tgt.push_back(v + BO);
-    for (int64_t v : L.upd_src) R.upd_src.push_back(v + BO);
-    const int64_t LLO = (int64_t)R.lvlL_rows.size(), ULO = (int64_t)R.lvlU_rows.size();
-    for (size_t i = 1; i < L.lvlL_ptr.size(); ++i) R.lvlL_ptr.push_back(L.lvlL_ptr[i] + LLO);
-    for (size_t i = 1; i < L.lvlU_ptr.size(); ++i) R.lvlU_ptr.push_back(L.lvlU_ptr[i] + ULO);
-    R.lvlL_rows.insert(R.lvlL_rows.end(), L.lvlL_rows.begin(), L.lvlL_rows.end());
-    R.lvlU_rows.insert(R.lvlU_rows.end(), L.lvlU_rows.begin(), L.lvlU_rows.end());
-    R.sd_lvlL.push_back((int64_t)R.lvlL_ptr.size() - 1);
-    R.sd_lvlU.push_back((int64_t)R.lvlU_ptr.size() - 1);
-    R.sd_row.push_back((int64_t)R.gnode.size());
+    const RasPlan& L = subs[s];
+    oR[s + 1] = oR[s] + (int64_t)L.gnode.size();
+    oB[s + 1] = oB[s] + (int64_t)L.col.size();
+    oL[s + 1] = oL[s] + (int64_t)L.lent_pos.size();
+    oU[s + 1] = oU[s] + (int64_t)L.upd_tgt.size();
+    oLR[s + 1] = oLR[s] + (int64_t)L.lvlL_rows.size();
+    oUR[s + 1] = oUR[s] + (int64_t)L.lvlU_rows.size();
+    oLP[s + 1] = oLP[s] + (int64_t)L.lvlL_ptr.size() - 1;
+    oUP[s + 1] = oUP[s] + (int64_t)L.lvlU_ptr.size() - 1;
     R.max_levels = std::max(R.max_levels, L.max_levels);
     R.max_rows = std::max(R.max_rows, L.max_rows);
+  }
+  R.gnode.resize(oR[np]);
+  R.owned.resize(oR[np]);
+  R.diag.resize(oR[np]);
+  R.row_ptr.assign(oR[np] + 1, 0);
+  R.lent_ptr.assign(oR[np] + 1, 0);
+  R.col.resize(oB[np]);
+  R.gblk.resize(oB[np]);
+  R.lent_pos.resize(oL[np]);
+  R.lent_kdiag.resize(oL[np]);
+  R.upd_ptr.assign(oL[np] + 1, 0);
+  R.upd_tgt.resize(oU[np]);
+  R.upd_src.resize(oU[np]);
+  R.lvlL_rows.resize(oLR[np]);
+  R.lvlU_rows.resize(oUR[np]);
+  R.lvlL_ptr.assign(oLP[np] + 1, 0);
+  R.lvlU_ptr.assign(oUP[np] + 1, 0);
+  R.sd_row.assign(oR.begin(), oR.end());
+  R.sd_lvlL.assign(oLP.begin(), oLP.end());
+  R.sd_lvlU.assign(oUP.begin(), oUP.end());
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int32_t s = 0; s < np; ++s) {
+    RasPlan& L = subs[s];
+    const int64_t RO = oR[s], BO = oB[s], LO = oL[s], UO = oU[s];
+    const int64_t rows = oR[s + 1] - RO;
+    for (int64_t i = 0; i < rows; ++i) {
+      R.gnode[RO + i] = L.gnode[i];
+      R.owned[RO + i] = L.owned[i];
+      R.diag[RO + i] = L.diag[i] + BO;
+      R.row_ptr[RO + i + 1] = L.row_ptr[i + 1] + BO;
+      R.lent_ptr[RO + i + 1] = L.lent_ptr[i + 1] + LO;
+    }
+    for (size_t k = 0; k < L.col.size(); ++k) {
+      R.col[BO + k] = (int32_t)(L.col[k] + RO);
+      R.gblk[BO + k] = L.gblk[k];
+    }
+    for (size_t e = 0; e < L.lent_pos.size(); ++e) {
+      R.lent_pos[LO + e] = L.lent_pos[e] + BO;
+      R.lent_kdiag[LO + e] = L.lent_kdiag[e] + BO;
+      R.upd_ptr[LO + e + 1] = L.upd_ptr[e + 1] + UO;
+    }
+    for (size_t u = 0; u < L.upd_tgt.size(); ++u) {
+      R.upd_tgt[UO + u] = L.upd_tgt[u] + BO;
+      R.upd_src[UO + u] = L.upd_src[u] + BO;
+    }
+    std::copy(L.lvlL_rows.begin(), L.lvlL_rows.end(), R.lvlL_rows.begin() + oLR[s]);
+    std::copy(L.lvlU_rows.begin(), L.lvlU_rows.end(), R.lvlU_rows.begin() + oUR[s]);
+    for (size_t i = 1; i < L.lvlL_ptr.size(); ++i) R.lvlL_ptr[oLP[s] + i] = L.lvlL_ptr[i] + oLR[s];
+    for (size_t i = 1; i < L.lvlU_ptr.size(); ++i) R.lvlU_ptr[oUP[s] + i] = L.lvlU_ptr[i] + oUR[s];
     L = RasPlan();  // release the per-subdomain memory early
   }
   R.np = np;
