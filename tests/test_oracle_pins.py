@@ -558,3 +558,15 @@ def test_wss_ignores_pressure_and_rigid_rotation():
     y3[:, 0:3] = np.cross(np.array([0.3, -1.2, 0.7]), m.X)
     _, w3, _, _ = O.wall_shear_stress(m.X, m.tets, m.tet_domain, m.node_problem, y3, 0.035)
     assert np.abs(w3).max() < 1e-13
+
+
+def test_wss_face_set_is_the_algorithm_1_interface():
+    """The oracle's inner-wall faces (a dictionary over sorted vertex triples) are
+    exactly the interface faces of the mesh generator's Algorithm 1 walk (a sort
+    of all faces), on a single tube and on a batch of three."""
+    parts = [vm.tube_config("tube-12x8x4"), vm.tube_mesh(6, 8, 2, 1, radius=0.6, length=2.0, seed=9)]
+    for m in parts + [vm.concat_meshes(parts)]:
+        faces = O.wss_faces(m.tets, m.tet_domain, m.node_problem)
+        mine = {tuple(sorted(int(m.tets[t, a]) for a in range(4) if a != f)) for t, f in faces}
+        ref = {tuple(sorted(int(v) for v in tri)) for tri in vm.interface_faces(m.tets, m.tet_domain)}
+        assert mine == ref and len(mine) == len(faces)
