@@ -232,6 +232,25 @@ class Problem:
         self.itf = itf
 
     # element-to-row placement --------------------------------------------------
+    @staticmethod
+    def route_fluid(Rm, Rc, Rh, itf):
+        """Node-row layout (T,4,7) of a fluid tet's residuals (Sec. 2.2, Eq. 6-7).
+
+        Continuity -> p row. Momentum -> u rows at fluid-only nodes; at interface
+        nodes (itf (T,4) bool) -> the d rows, where it is added to the wall
+        momentum of the wall tets: with one test function shared by both sides,
+        the boundary terms of the two weak forms cancel exactly when
+        sigma_s n_s = -sigma_f n_f (the traction balance of Sec. 2.1), so the sum
+        imposes it weakly. Mesh motion -> d rows at fluid-only nodes. The u rows of
+        interface nodes hold the kinematic condition instead (constraint rows).
+        """
+        itf = itf[:, :, None]
+        out = np.zeros(Rm.shape[:2] + (7,), dtype=np.result_type(Rm, Rc, Rh))
+        out[:, :, 0:3] = np.where(itf, 0.0, Rm)
+        out[:, :, 3] = Rc
+        out[:, :, 4:7] = np.where(itf, Rm, Rh)
+        return out
+
     def element_rows(self, y, y1, y2):
         """Per-tet contributions (T_f,4,7) and (T_w,4,7) in the node-row layout.
 
@@ -247,11 +266,7 @@ class Problem:
             Xe = X[ft]
             Rm, Rc, Rh = fluid_element(Xe, y[ft, 0:3], y[ft, 3], y[ft, 4:7], y1[ft, 0:3],
                                        y1[ft, 4:7], self.mat, self.dt, self.stab)
-            itf = self.itf[ft][:, :, None]
-            out_f = np.zeros(ft.shape + (7,), dtype=Rm.dtype)
-            out_f[:, :, 0:3] = np.where(itf, 0.0, Rm)
-            out_f[:, :, 3] = Rc
-            out_f[:, :, 4:7] = np.where(itf, Rm, Rh)
+            out_f = self.route_fluid(Rm, Rc, Rh, self.itf[ft])
         if len(wt):
             Rw = wall_element(X[wt], y[wt, 4:7], y1[wt, 4:7], y2[wt, 4:7], self.mat, self.dt)
             out_w = np.zeros(wt.shape + (7,), dtype=Rw.dtype)
@@ -341,11 +356,7 @@ class Problem:
         if which == 0:
             Rm, Rc, Rh = fluid_element(X[tets], ye[:, :, 0:3], ye[:, :, 3], ye[:, :, 4:7],
                                        y1[tets, 0:3], y1[tets, 4:7], self.mat, self.dt, self.stab)
-            itf = self.itf[tets][:, :, None]
-            out = np.zeros(tets.shape + (7,), dtype=np.complex128)
-            out[:, :, 0:3] = np.where(itf, 0.0, Rm)
-            out[:, :, 3] = Rc
-            out[:, :, 4:7] = np.where(itf, Rm, Rh)
+            out = self.route_fluid(Rm, Rc, Rh, self.itf[tets])
         else:
             Rw = wall_element(X[tets], ye[:, :, 4:7], y1[tets, 4:7], y2[tets, 4:7], self.mat, self.dt)
             out = np.zeros(tets.shape + (7,), dtype=np.complex128)

@@ -570,3 +570,137 @@ def test_wss_face_set_is_the_algorithm_1_interface():
         mine = {tuple(sorted(int(m.tets[t, a]) for a in range(4) if a != f)) for t, f in faces}
         ref = {tuple(sorted(int(v) for v in tri)) for tri in vm.interface_faces(m.tets, m.tet_domain)}
         assert mine == ref and len(mine) == len(faces)
+
+
+# ---------------------------------------------------------------------------
+# interface traction balance through the coupled rows (Sec. 2.1 interface
+# conditions, Sec. 2.2 Eq. 6-7): a pressurised lumen loads the wall only through
+# the fluid momentum that the interface d rows receive
+# ---------------------------------------------------------------------------
+def _coupled_lame(n_theta, n_rw):
+    """Coupled ring under a lumen at rest with uniform pressure P.
+
+    Fluid and wall of a short tube segment; u is held at 0 and p at P by leaving
+    their rows and columns out of the solve, and the d unknowns are solved from
+    the oracle's own d rows: wall momentum at wall nodes, fluid + wall momentum at
+    interface nodes, harmonic mesh motion at fluid-only nodes. The end planes are
+    axial rollers (d_z = 0) and the x = 0 / y = 0 planes symmetry planes, so the
+    wall is in plane strain, which is the Lame closed form's setting. dt is huge
+    and the previous levels are the reference state, so inertia and the mesh
+    velocity vanish. The fluid's traction reaches the wall only through the
+    interface routing: nothing else puts a load on it.
+    """
+    g = GOLDEN["lame"]
+    a, b, Pp = g["a"], g["b"], g["P"]
+    mat = dict(MAT, E_s=g["E"], nu_s=g["nu"])
+    L = 0.2
+    m = vm.tube_mesh(2, n_theta, 2, n_rw, radius=a, length=L, wall=b - a, jitter=0.0)
+    tag = m.node_tag & ~np.uint32(vm.INLET | vm.OUTLET | vm.WALL_END)   # the test sets its own ends
+    P = O.Problem(m.X, m.tets, m.tet_domain, tag, m.node_problem, m.inlets, mat=mat, dt=1e8)
+    N = m.n_nodes
+    fl = (tag & vm.FLUID) != 0
+    y = np.zeros((N, 7))
+    y[fl, 3] = Pp
+    yref = y.copy()
+    z = m.X[:, 2]
+    rr = np.hypot(m.X[:, 0], m.X[:, 1])
+    th = np.arctan2(m.X[:, 1], m.X[:, 0])
+    axis = rr < 1e-12
+    fix = np.zeros((N, 3), dtype=bool)
+    fix[:, 2] = (z < 1e-12) | (z > L - 1e-12)
+    fix[:, 0] = axis | np.isclose(np.abs(np.cos(th)), 0.0, atol=1e-9)
+    fix[:, 1] = axis | np.isclose(np.abs(np.sin(th)), 0.0, atol=1e-9)
+    dof = (7 * np.arange(N)[:, None] + np.arange(4, 7)[None, :])[~fix]
+    load = None
+    for _ in range(8):
+        F = P.residual(y, yref, yref, 1.0).reshape(-1)[dof]
+        if load is None:
+            load = np.linalg.norm(F)
+        if np.linalg.norm(F) <= 1e-11 * load:
+            break
+        J = P.jacobian(y, yref, yref, 1.0)[dof][:, dof].tocsc()
+        import scipy.sparse.linalg as spla
+        yv = y.reshape(-1)
+        yv[dof] -= spla.spsolve(J, F)
+        y = yv.reshape(N, 7)
+    d = y[:, 4:7]
+    ur = np.where(axis, 0.0, (d[:, 0] * m.X[:, 0] + d[:, 1] * m.X[:, 1]) / np.where(axis, 1.0, rr))
+    return ur[np.isclose(rr, a)].mean(), ur[np.isclose(rr, b)].mean()
+
+
+def test_interface_traction_balance_coupled_lame():
+    """The wall displacement under the fluid's pressure converges at O(h^2) to
+    the plane-strain Lame values u_r(a) = 8.458e-5 cm, u_r(b) = 7.250e-5 cm: the
+    fluid momentum that the interface d rows receive is the traction -sigma_f n_f
+    = P n_f that the wall must balance (sigma_s n_s = -sigma_f n_f, Sec. 2.1)."""
+    g = GOLDEN["lame"]
+    ua1, ub1 = _coupled_lame(16, 2)
+    ua2, ub2 = _coupled_lame(32, 4)
+    ea1, ea2 = abs(ua1 - g["u_r_a"]), abs(ua2 - g["u_r_a"])
+    eb1, eb2 = abs(ub1 - g["u_r_b"]), abs(ub2 - g["u_r_b"])
+    assert ua2 > 0 and ub2 > 0
+    assert ea2 < ea1 / 3.0 and eb2 < eb1 / 3.0, (ua1, ua2, ub1, ub2)
+    assert ea2 / g["u_r_a"] < 0.02 and eb2 / g["u_r_b"] < 0.02, (ua2, ub2)
+
+
+@pytest.mark.parametrize("mutation", ["dropped", "flipped", "to_u_rows"])
+def test_interface_traction_pin_catches_wrong_routing(monkeypatch, mutation):
+    """A routing that drops the fluid momentum at interface nodes, flips its sign
+    or sends it to the u rows fails the coupled Lame pin (the mistake is planted in
+    the oracle, on the CPU)."""
+    def routed(Rm, Rc, Rh, itf):
+        i3 = itf[:, :, None]
+        out = np.zeros(Rm.shape[:2] + (7,), dtype=np.result_type(Rm, Rc, Rh))
+        out[:, :, 3] = Rc
+        if mutation == "dropped":
+            out[:, :, 0:3] = np.where(i3, 0.0, Rm)
+            out[:, :, 4:7] = np.where(i3, 0.0, Rh)
+        elif mutation == "flipped":
+            out[:, :, 0:3] = np.where(i3, 0.0, Rm)
+            out[:, :, 4:7] = np.where(i3, -Rm, Rh)
+        else:
+            out[:, :, 0:3] = Rm
+            out[:, :, 4:7] = np.where(i3, 0.0, Rh)
+        return out
+
+    monkeypatch.setattr(O.Problem, "route_fluid", staticmethod(routed))
+    g = GOLDEN["lame"]
+    ua, ub = _coupled_lame(16, 2)
+    assert abs(ua - g["u_r_a"]) / g["u_r_a"] > 0.5 and abs(ub - g["u_r_b"]) / g["u_r_b"] > 0.5, (ua, ub)
+
+
+# ---------------------------------------------------------------------------
+# inflow waveform (Eq. 3 inlet condition u_f = v_f^d; the workloads' pulsatile
+# waveform with period 0.8 s)
+# ---------------------------------------------------------------------------
+def test_inlet_waveform_and_profile():
+    """U(t) = 30 (1 + 0.5 sin(2 pi t/0.8)) at t = 0, T/8, T/4, T/2, 3T/4 where the
+    sine takes the values 0, sqrt2/2, 1, 0, -1; the parabola is U on the axis, 3U/4
+    at r = R/2 and 0 from r = R on; the direction is the inlet normal."""
+    g = GOLDEN["inlet_waveform"]
+    R = g["R"]
+    n = np.array([0.0, 0.6, 0.8])
+    e1 = np.array([1.0, 0.0, 0.0])
+    c = np.array([0.3, -0.2, 1.0])
+    inlet = dict(center=c, normal=n, radius=R, peak=g["peak"], amp=g["amp"], freq=1.0 / g["period"], phase=0.0)
+    X = np.stack([c + 2.0 * n, c + 0.5 * R * e1 - 1.0 * n, c + R * e1, c + 1.5 * R * e1])
+    for t, U in g["t_U"]:
+        u = O.inlet_profile(X, inlet, t)
+        assert np.allclose(u[0], U * n, rtol=1e-13, atol=1e-12), (t, u[0], U)
+        assert np.allclose(u[1], g["profile_half_radius"] * U * n, rtol=1e-13, atol=1e-12)
+        assert np.all(u[2:] == 0.0)
+
+
+def test_inlet_rows_use_the_waveform_at_the_step_end():
+    """The inlet constraint rows of F(y) hold u - u_in(t) at the time the step
+    ends: at y = 0 an inlet node on the axis has F_u = -U(t) n."""
+    g = GOLDEN["inlet_waveform"]
+    m = vm.tube_mesh(2, 4, 1, 1, radius=0.5, length=1.0, jitter=0.0, peak=g["peak"], amp=g["amp"],
+                     freq=1.0 / g["period"])
+    P = make_problem(m)
+    on_axis = (np.hypot(m.X[:, 0], m.X[:, 1]) < 1e-12) & ((m.node_tag & vm.INLET) != 0)
+    assert on_axis.sum() == 1
+    y = np.zeros((m.n_nodes, 7))
+    for t, U in g["t_U"]:
+        F = P.residual(y, y, y, t)
+        assert np.allclose(F[on_axis, 0:3], [0.0, 0.0, -U], rtol=1e-13, atol=1e-12), (t, F[on_axis])
