@@ -54,41 +54,59 @@ class Mesh:
         return len(self.inlets)
 
 
-def interface_faces(tets, tet_domain):
-    """Algorithm 1 (Sec. 4.8): faces of fluid tets shared with a wall tet.
+def match_faces(tets):
+    """Pair up the faces of a conforming tet mesh.
 
-    Faces are matched by their sorted vertex triple. Returns an (F,3) int64 array
-    of vertex ids, oriented as in the fluid tetrahedron.
+    Returns (faces, partner): faces (4T,3) int64 vertex triples oriented as in
+    their tetrahedron (face f of tet t is row 4t+f and omits vertex f), and
+    partner (4T,) the row of the same triangle in the neighbouring tet, or -1
+    on the boundary. Faces are matched by their sorted vertex triple, sorted on
+    two integer keys (first two vertices combined, then the third).
     """
     tets = np.asarray(tets, dtype=np.int64)
-    T = tets.shape[0]
-    faces = tets[:, TET_FACES]                      # (T,4,3)
-    key = np.sort(faces, axis=2).reshape(-1, 3)
-    owner = np.repeat(np.arange(T), 4)
-    order = np.lexsort((key[:, 2], key[:, 1], key[:, 0]))
-    ks = key[order]
-    same = np.all(ks[1:] == ks[:-1], axis=1)
+    faces = tets[:, TET_FACES].reshape(-1, 3)
+    key = np.sort(faces, axis=1)
+    n = int(key.max()) + 1 if key.size else 1
+    k01 = key[:, 0] * n + key[:, 1]
+    order = np.lexsort((key[:, 2], k01))
+    same = (k01[order[1:]] == k01[order[:-1]]) & (key[order[1:], 2] == key[order[:-1], 2])
+    partner = -np.ones(len(faces), dtype=np.int64)
     i0 = order[:-1][same]
     i1 = order[1:][same]
-    d0 = tet_domain[owner[i0]]
-    d1 = tet_domain[owner[i1]]
-    out = []
-    m = (d0 == 0) & (d1 == 1)
-    out.append(faces.reshape(-1, 3)[i0[m]])
-    m = (d0 == 1) & (d1 == 0)
-    out.append(faces.reshape(-1, 3)[i1[m]])
-    return np.concatenate(out, axis=0)
+    partner[i0] = i1
+    partner[i1] = i0
+    return faces, partner
 
 
-def tag_nodes(n_nodes, tets, tet_domain):
+def interface_faces(tets, tet_domain, matched=None):
+    """Algorithm 1 (Sec. 4.8): faces of fluid tets shared with a wall tet.
+
+    Returns an (F,3) int64 array of vertex ids, oriented as in the fluid
+    tetrahedron, in increasing order of (fluid tet, face). matched: the output
+    of match_faces(tets), if already at hand.
+    """
+    faces, partner = match_faces(tets) if matched is None else matched
+    dom = np.asarray(tet_domain)
+    own = np.arange(len(faces)) // 4
+    sel = (partner >= 0) & (dom[own] == 0)
+    sel[sel] = dom[partner[sel] // 4] == 1
+    return faces[sel]
+
+
+def tag_nodes(n_nodes, tets, tet_domain, matched=None):
     """FLUID / WALL / INTERFACE flags from the tet domains and Algorithm 1."""
     tag = np.zeros(n_nodes, dtype=np.uint32)
     tets = np.asarray(tets, dtype=np.int64)
-    tag[np.unique(tets[tet_domain == 0])] |= FLUID
-    tag[np.unique(tets[tet_domain == 1])] |= WALL
-    f = interface_faces(tets, tet_domain)
+    dom = np.asarray(tet_domain)
+    for d, bit in ((0, FLUID), (1, WALL)):
+        mark = np.zeros(n_nodes, dtype=bool)
+        mark[tets[dom == d].ravel()] = True
+        tag[mark] |= bit
+    f = interface_faces(tets, tet_domain, matched)
     if f.size:
-        tag[np.unique(f)] |= INTERFACE
+        mark = np.zeros(n_nodes, dtype=bool)
+        mark[f.ravel()] = True
+        tag[mark] |= INTERFACE
     return tag
 
 

@@ -1,6 +1,7 @@
 """Kuhn-voxel meshes: a plain box (test meshes) and the bifurcating tree."""
 import numpy as np
-from .mesh import Mesh, FLUID, WALL, INTERFACE, INLET, OUTLET, WALL_END, OUTER, orient_positive, tag_nodes
+from .mesh import (Mesh, FLUID, WALL, INTERFACE, INLET, OUTLET, WALL_END, OUTER, orient_positive, tag_nodes,
+                   match_faces)
 
 _PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 
@@ -103,7 +104,8 @@ def _branch_distance(pts, b, flat_start, flat_end):
     rel = pts - b["p0"]
     t = rel @ d
     tc = np.clip(t, 0.0, L)
-    dist = np.linalg.norm(rel - tc[:, None] * d[None, :], axis=1)
+    v = rel - tc[:, None] * d[None, :]
+    dist = np.sqrt(np.add.reduce(v * v, axis=1))
     if flat_start:
         dist = np.where(t < 0.0, np.inf, dist)
     if flat_end:
@@ -132,12 +134,14 @@ def tree_mesh(generations=3, r0=1.2, ratio=0.79, ratio_noise=0.0, angle=(35.0, 6
     n = np.ceil((hi - lo) / h).astype(np.int64)
     # candidate cubes per branch (bounding box of the dilated capsule)
     cubes = []
+    boxes = []
     for i, b in enumerate(br):
         R = b["radius"] + wall + h
         bl = np.minimum(b["p0"], b["p1"]) - R
         bh = np.maximum(b["p0"], b["p1"]) + R
         i0 = np.maximum(np.floor((bl - lo) / h).astype(np.int64), 0)
         i1 = np.minimum(np.ceil((bh - lo) / h).astype(np.int64), n)
+        boxes.append((i0, i1))
         gx, gy, gz = np.meshgrid(np.arange(i0[0], i1[0]), np.arange(i0[1], i1[1]), np.arange(i0[2], i1[2]),
                                  indexing="ij")
         c = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
@@ -145,7 +149,10 @@ def tree_mesh(generations=3, r0=1.2, ratio=0.79, ratio_noise=0.0, angle=(35.0, 6
         dist = _branch_distance(ctr, b, b["parent"] < 0, b["leaf"])
         keep = dist < b["radius"] + wall + 0.9 * h
         cubes.append(c[keep])
-    cubes = np.unique(np.concatenate(cubes), axis=0)
+    cubes = np.concatenate(cubes)
+    # distinct cubes in lexicographic (x, y, z) order, through one integer key
+    ckey = np.unique(cubes[:, 2] + n[2] * (cubes[:, 1] + n[1] * cubes[:, 0]))
+    cubes = np.stack([ckey // (n[1] * n[2]), (ckey // n[2]) % n[1], ckey % n[2]], axis=1)
     # Kuhn tets of the candidate cubes, vertex ids on the global grid
     def gid(ix, iy, iz):
         return (iz * (n[1] + 1) + iy) * (n[0] + 1) + ix
@@ -166,9 +173,17 @@ def tree_mesh(generations=3, r0=1.2, ratio=0.79, ratio_noise=0.0, angle=(35.0, 6
         iz = g // ((n[0] + 1) * (n[1] + 1))
         return lo + np.stack([ix, iy, iz], axis=1) * h
     ctr = sum(coords(tv[:, a]) for a in range(4)) / 4.0
+    # a centroid outside a branch's box of cubes is farther than radius + wall + h
+    # from that branch, so each branch is measured only on the tets of its box
+    # (tet p * nc + c lies in cube c; the cubes are sorted by x first)
+    nc = len(cubes)
     gap = np.full(len(tv), np.inf)
-    for b in br:
-        gap = np.minimum(gap, _branch_distance(ctr, b, b["parent"] < 0, b["leaf"]) - b["radius"])
+    for b, (i0, i1) in zip(br, boxes):
+        a0, a1 = np.searchsorted(cubes[:, 0], [i0[0], i1[0]])
+        cs = np.arange(a0, a1)
+        cs = cs[(cubes[cs, 1] >= i0[1]) & (cubes[cs, 1] < i1[1]) & (cubes[cs, 2] >= i0[2]) & (cubes[cs, 2] < i1[2])]
+        sel = (np.arange(6)[:, None] * nc + cs[None, :]).ravel()
+        gap[sel] = np.minimum(gap[sel], _branch_distance(ctr[sel], b, b["parent"] < 0, b["leaf"]) - b["radius"])
     fluid = gap < 0.0
     wallm = (~fluid) & (gap < wall)
     keep = fluid | wallm
@@ -180,14 +195,12 @@ def tree_mesh(generations=3, r0=1.2, ratio=0.79, ratio_noise=0.0, angle=(35.0, 6
     X = coords(ids)
     tets = orient_positive(X, tets).astype(np.int32)
     N = len(ids)
-    tag = tag_nodes(N, tets, dom)
+    matched = match_faces(tets)
+    tag = tag_nodes(N, tets, dom, matched)
     # caps: fluid boundary faces that are not interface faces
-    from .mesh import TET_FACES
-    faces = tets.astype(np.int64)[:, TET_FACES].reshape(-1, 3)
-    owner = np.repeat(np.arange(len(tets)), 4)
-    key = np.sort(faces, axis=1)
-    _, finv, fcnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
-    bnd = fcnt[finv.ravel()] == 1
+    faces, partner = matched
+    owner = np.arange(len(faces)) // 4
+    bnd = partner < 0
     fl = (tag & FLUID) != 0
     wl = (tag & WALL) != 0
     fb = faces[bnd & (dom[owner] == 0)]
