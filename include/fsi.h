@@ -125,7 +125,9 @@ typedef struct {
   int32_t threads_per_row;/* BSR SpMV mapping: 32 = one warp per block row, 16 = two rows per warp */
   int32_t ordering;       /* node order inside each subdomain (Sec. 4.5): 0 natural
                              (global node order), 1 RCM, 2 RCM with lumen nodes
-                             before interface and wall nodes */
+                             before interface and wall nodes, 3 nested dissection
+                             (coordinate bisection, up to 3 levels, RCM inside each
+                             part; the parts of one level are solved side by side) */
   int32_t factor_mode;    /* shared-memory use of the ILU factorisation: 0 automatic
                              (= 3, the fastest measured); 1 pivots and update sources
                              prefetched into shared memory, 2 sources only, 3 neither
@@ -136,6 +138,14 @@ typedef struct {
   int32_t fault_test;     /* tests only: 1 = the preconditioner apply's copy engine
                              issues nothing, so the apply's bounded wait runs out and
                              the call returns FSI_ERR_TIMEOUT; 0 otherwise */
+  int32_t apply_mode;     /* preconditioner apply kernel: 0 automatic (the streamed
+                             apply when its shared-memory footprint fits, else the
+                             level-scheduled one); 1 streamed (FSI_ERR_ARG if it does
+                             not fit); 2 level-scheduled. Same arithmetic, same result
+                             up to the order of the row sums. */
+  int32_t stage_blocks;   /* streamed apply: factor blocks per ring stage, 0 = automatic
+                             (sized so that every subdomain's CTA is resident) */
+  int32_t stages;         /* streamed apply: ring stages in flight, 2..8, 0 = automatic (3) */
 } fsi_options;
 
 typedef struct {
@@ -170,6 +180,8 @@ typedef struct {
   int32_t max_levels;          /* deepest level schedule over the subdomains */
   int64_t device_bytes;        /* device memory held by the context */
   int64_t n_wss_faces;         /* inner-wall faces (fluid tet against wall tet) */
+  int32_t nd_depth;            /* deepest nested dissection of a subdomain (ordering 3), else 0 */
+  int32_t apply_kernel;        /* preconditioner apply in use: 1 streamed, 2 level-scheduled */
 } fsi_info;
 
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,

@@ -18,8 +18,9 @@ mesh node) and a vector r:
 2. Overlap (Omega_i^delta, Sec. 3): delta layers of graph neighbours, the graph
    being "two nodes share a tetrahedron".
 3. Order of each overlapped subdomain (Sec. 4.5): natural (node number), reverse
-   Cuthill-McKee, or reverse Cuthill-McKee stably sorted by a node rank (lumen,
-   interface, wall). Cuthill-McKee here: start at the unvisited node of least
+   Cuthill-McKee, reverse Cuthill-McKee stably sorted by a node rank (lumen,
+   interface, wall), or nested dissection (see nested_dissection) with reverse
+   Cuthill-McKee inside every part. Cuthill-McKee here: start at the unvisited node of least
    degree (ties: lowest node number), move the start to the last node reached by
    a breadth-first search that visits neighbours in increasing node number, then
    number breadth first, each node's unnumbered neighbours by increasing
@@ -133,11 +134,60 @@ def rcm(nodes, adj):
     return np.array(order[::-1], dtype=np.int64)
 
 
-def subdomain_order(nodes, adj, ordering, node_rank=None):
+ND_MIN_LEAF = 48
+
+
+def nested_dissection(nodes, adj, X):
+    """Nested-dissection items of an overlapped subdomain (Sec. 4.5's ND).
+
+    Depth D: the largest D <= 3 with |nodes| >= 48 * 2^D. Each piece is cut at
+    the median of its longest coordinate axis: ordered by (coordinate, node
+    number), the lower floor(n/2) nodes form the lower half; the separator is the
+    set of lower-half nodes with a graph neighbour in the upper half, the rest of
+    the lower half and the upper half are the two children. Returns the items in
+    phase-major order (the 2^D leaves left to right, then the separators from the
+    deepest level up to the root's), each a list of node numbers, and D. No edge
+    joins two items of the same phase.
+    """
+    X = np.asarray(X)
+    m = len(nodes)
+    D = 0
+    while D < 3 and m >= ND_MIN_LEAF * 2 ** (D + 1):
+        D += 1
+    cur = [[int(v) for v in nodes]]
+    seps = []
+    for _ in range(D):
+        nxt, lvl = [], []
+        for S in cur:
+            if S:
+                ext = X[S].max(axis=0) - X[S].min(axis=0)
+                ax = int(np.argmax(ext))
+            else:
+                ax = 0
+            S = sorted(S, key=lambda v: (X[v, ax], v))
+            half = len(S) // 2
+            upper = set(S[half:])
+            sep = [v for v in S[:half] if any(int(w) in upper for w in adj[v])]
+            sset = set(sep)
+            nxt += [[v for v in S[:half] if v not in sset], S[half:]]
+            lvl.append(sep)
+        cur = nxt
+        seps.append(lvl)
+    items = list(cur)
+    for lvl in reversed(seps):
+        items += lvl
+    return items, D
+
+
+def subdomain_order(nodes, adj, ordering, node_rank=None, X=None):
     """Local order of an overlapped subdomain: 0 natural, 1 RCM, 2 RCM stably
-    sorted by node_rank."""
+    sorted by node_rank, 3 nested dissection with RCM inside every item."""
     if ordering == 0:
         return np.array(sorted(int(v) for v in nodes), dtype=np.int64)
+    if ordering == 3:
+        items, _ = nested_dissection(nodes, adj, X)
+        parts = [rcm(np.array(it, dtype=np.int64), adj) for it in items]
+        return np.concatenate(parts) if parts else np.zeros(0, dtype=np.int64)
     order = rcm(nodes, adj)
     if ordering == 2:
         order = order[np.argsort(np.asarray(node_rank)[order], kind="stable")]
@@ -208,7 +258,7 @@ class RAS:
             if len(own) == 0:
                 continue
             nodes = overlap(own, adj, delta)
-            order = subdomain_order(nodes, adj, ordering, node_rank)
+            order = subdomain_order(nodes, adj, ordering, node_rank, X)
             keep = ilu_levels(order, adj, fill) <= fill
             m = len(order)
             dofs = (7 * order[:, None] + np.arange(7)[None, :]).reshape(-1)

@@ -484,6 +484,9 @@ void fill_defaults(fsi_options* o) {
   o->verbose = 0;
   o->fault_test = 0;
   o->factor_mode = 0;
+  o->apply_mode = 0;
+  o->stage_blocks = 0;
+  o->stages = 0;
 }
 
 }  // namespace
@@ -522,11 +525,17 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (q.jac_lag > 0) o.jac_lag = q.jac_lag;
       if (q.ilu_level >= 0) o.ilu_level = q.ilu_level;
       o.threads_per_row = (q.threads_per_row == 16) ? 16 : 32;
-      if (q.ordering >= 0 && q.ordering <= 2) o.ordering = q.ordering;
+      if (q.ordering >= 0 && q.ordering <= 3) o.ordering = q.ordering;
       o.verbose = q.verbose;
       o.fault_test = q.fault_test;
       if (q.factor_mode >= 0 && q.factor_mode <= 3) o.factor_mode = q.factor_mode;
+      o.apply_mode = q.apply_mode;
+      o.stage_blocks = q.stage_blocks;
+      o.stages = q.stages;
     }
+    if (o.apply_mode < 0 || o.apply_mode > 2) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0, 1 or 2"};
+    if (o.stage_blocks < 0) throw StatusError{FSI_ERR_ARG, "stage_blocks must be >= 0"};
+    if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) throw StatusError{FSI_ERR_ARG, "stages must be 0 or 2..8"};
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
     if (o.ilu_level < 0 || o.ilu_level > 3) throw StatusError{FSI_ERR_ARG, "ilu_level must be 0..3"};
     if (o.gmres_restart > 64) throw StatusError{FSI_ERR_ARG, "gmres_restart must be <= 64"};
@@ -855,7 +864,35 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       }
       Loff[R.np] = (int64_t)Lsrc.size();
       Uoff[R.np] = (int64_t)Usrc.size();
+      // per nested-dissection item: its first / end block in the subdomain's L
+      // stream (rows ascending) and U stream (rows descending)
+      std::vector<int32_t> iblk(4 * R.item_row.size());
+      for (int32_t sd = 0; sd < R.np; ++sd) {
+        const int64_t a = R.sd_row[sd], b = R.sd_row[sd + 1];
+        int64_t Ltot = 0, Utot = 0;
+        for (int64_t q = a; q < b; ++q) Utot += Ucnt[q];
+        int64_t row = 0;
+        for (int64_t k = R.sd_item[sd]; k < R.sd_item[sd + 1]; ++k) {
+          const int64_t end = R.item_row[k];
+          int64_t Lb = 0, Ub = 0;  // blocks of rows [row, end)
+          for (int64_t q = a + row; q < a + end; ++q) Lb += Lcnt[q], Ub += Ucnt[q];
+          int64_t Uafter = 0;      // U blocks of rows at and after `end` (they come first)
+          for (int64_t q = a + end; q < b; ++q) Uafter += Ucnt[q];
+          iblk[4 * k + 0] = (int32_t)Ltot;
+          iblk[4 * k + 1] = (int32_t)(Ltot + Lb);
+          iblk[4 * k + 2] = (int32_t)Uafter;
+          iblk[4 * k + 3] = (int32_t)(Uafter + Ub);
+          Ltot += Lb;
+          row = end;
+        }
+        (void)Utot;
+      }
       RasStreamDev& rs = cp->rs;
+      rs.sd_depth = cp->upload(R.sd_depth);
+      rs.sd_item = cp->upload(R.sd_item);
+      rs.item_row = cp->upload(R.item_row);
+      rs.item_blk = cp->upload(iblk);
+      rs.max_depth = R.max_depth;
       rs.np = R.np;
       rs.sd_row = rd.sd_row;
       rs.gnode = rd.gnode;
@@ -872,23 +909,26 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Ucol = cp->upload(Ucol);
       // stage geometry: NST stages of SB blocks. The subdomains should all be
       // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
-      // shared memory per CTA leaves after the vector; FSI_STAGE_BLOCKS /
-      // FSI_STAGES override (tuning)
+      // shared memory per CTA leaves after the vector; the stage_blocks and
+      // stages options override the choice
       const int vsz = cp->mixed ? 4 : 8, stride = cp->mixed ? 52 : 50;
-      int nst = 3;
+      int nst = o.stages > 0 ? o.stages : 3;
+      const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
       const int64_t per_sm = std::min<int64_t>(8, (R.np + 151) / 152);
-      const int64_t fixed = 128 + 7 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
-      int64_t SB = ((int64_t)(227 * 1024) / per_sm - fixed) / (nst * stride * vsz);
-      SB = std::max<int64_t>(16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
-      if (const char* e = std::getenv("FSI_STAGE_BLOCKS")) SB = std::max(1, std::atoi(e));
-      if (const char* e = std::getenv("FSI_STAGES")) nst = std::min(8, std::max(2, std::atoi(e)));
+      const int64_t fixed = 128 * ((W * 64 + 127) / 128) + 7 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
+      int64_t SB = ((int64_t)(227 * 1024) / per_sm - fixed) / (W * nst * stride * vsz);
+      SB = std::max<int64_t>(W > 1 ? 8 : 16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
+      if (o.stage_blocks > 0) SB = o.stage_blocks;
       (void)maxblk;
       rs.nst = nst;
       rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
-      cp->use_stream = sm <= 200 * 1024;
+      const bool fits = sm <= 200 * 1024;
+      if (o.apply_mode == 1 && !fits)
+        throw StatusError{FSI_ERR_ARG, "apply_mode 1: the streamed apply's shared memory does not fit"};
+      cp->use_stream = o.apply_mode == 2 ? false : fits;
       if (cp->use_stream) {
         CK(cp->mixed ? ras_stream_init<float>(rs) : ras_stream_init<double>(rs));
         rs.Lpack = cp->dalloc<char>((int64_t)(stride * vs) * std::max<int64_t>(rs.nL, 1));
@@ -1178,6 +1218,8 @@ fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
   info->max_levels = c->plan.max_levels;
   info->device_bytes = c->dev_bytes;
   info->n_wss_faces = c->nwss;
+  info->nd_depth = c->plan.max_depth;
+  info->apply_kernel = c->use_stream ? 1 : 2;
   return FSI_OK;
 }
 

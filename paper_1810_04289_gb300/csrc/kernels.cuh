@@ -114,8 +114,14 @@ struct RasStreamDev {
   const int32_t* Ucol;
   int32_t stage_blocks;   // blocks per ring stage (one bulk copy; rows may straddle stages)
   int64_t max_rows;       // rows of the largest subdomain
-  int32_t nst;            // ring stages in flight (2..8)
+  int32_t nst;            // ring stages in flight per warp (2..8)
   int32_t stall;          // tests only: the producer issues nothing (bounded waits run out)
+  // nested-dissection items (one item per subdomain for the other orderings)
+  const int32_t* sd_depth;  // [np] depth D: 2^(D+1) - 1 items, solved by 2^D warps
+  const int64_t* sd_item;   // [np+1] first item of each subdomain
+  const int64_t* item_row;  // [items] end row of each item (subdomain-relative)
+  const int32_t* item_blk;  // [items][4] first / end block of the item in the subdomain's L and U streams
+  int32_t max_depth;        // deepest D (the CTA has 2^max_depth warps)
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);

@@ -119,38 +119,92 @@ __device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w
   return acc;
 }
 
+// One warp's stream of factor stages. The warp walks, in order, the segments of
+// the items it solves: forward phases 0..D (its item's L blocks), then backward
+// phases D..0 (its item's U blocks). Lane 0 keeps NST bulk copies in flight
+// along that sequence, into the warp's own ring, across phase boundaries (the
+// factor bytes do not depend on the solve, so the next phase's first stages
+// arrive while the CTA waits at the phase barrier).
+struct WarpFeed {
+  int D, wi;         // nested-dissection depth of the subdomain, warp index
+  int seg;           // producer: current segment 0 .. 2D+1, block offset in it
+  int off;
+  int issued, used;  // stages issued / consumed by this warp
+};
+
+// item of segment j for warp wi, or -1 when the warp has no item in that phase
+__device__ __forceinline__ int seg_item(int D, int wi, int j) {
+  const int p = j <= D ? j : 2 * D + 1 - j;
+  if (wi >= (1 << (D - p))) return -1;
+  return (1 << (D + 1)) - (1 << (D - p + 1)) + wi;
+}
+
+template <class TF, int STR>
+__device__ __forceinline__ void feed_issue(WarpFeed& f, const RasStreamDev& R, const int32_t* ib, const TF* Lpack,
+                                           const TF* Upack, TF* ring, uint64_t* full, int NST, int SB) {
+  while (f.seg <= 2 * f.D + 1) {
+    const int it = seg_item(f.D, f.wi, f.seg);
+    if (it >= 0) {
+      const bool isL = f.seg <= f.D;
+      const int b0 = ib[4 * it + (isL ? 0 : 2)], b1 = ib[4 * it + (isL ? 1 : 3)];
+      if (b0 + f.off < b1) {
+        const int nb = min(SB, b1 - b0 - f.off);
+        const int st = f.issued % NST;
+        const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&full[st], bytes);
+        bulk_g2s(ring + (size_t)st * SB * STR, (isL ? Lpack : Upack) + (size_t)(b0 + f.off) * STR, bytes,
+                 &full[st]);
+        f.off += nb;
+        f.issued++;
+        return;
+      }
+    }
+    f.seg++;
+    f.off = 0;
+  }
+}
+
+// Multi-warp streamed RAS apply (Sec. 3, Eq. 16) on nested-dissection ordered
+// subdomains (Sec. 4.5): one CTA per subdomain; in each phase of the forward
+// solve (leaves, then the separators level by level up to the root's) every item
+// of the phase is solved by its own warp, the items of a phase being independent
+// (no edge and no fill between them); the backward solve runs the phases in
+// reverse. Subdomains in the other orderings are one item (depth 0): one warp.
+// Each warp is its own producer: lane 0 streams the packed factor blocks of the
+// warp's items through a ring of NST stages of SB blocks (cp.async.bulk with
+// mbarrier completion); the warp solves the rows of the current stage (rows may
+// straddle stages) on the subdomain vector in shared memory.
 template <class TF>
-__global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const double* __restrict__ rin,
-                                                         double* __restrict__ z, float* __restrict__ z32,
-                                                         int32_t* err, const int* __restrict__ guard) {
+__global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const double* __restrict__ rin,
+                                                          double* __restrict__ z, float* __restrict__ z32,
+                                                          int32_t* err, const int* __restrict__ guard) {
   if (guard && *guard == 0) return;
   constexpr int STR = Pack<TF>::stride;
   extern __shared__ __align__(128) unsigned char smem[];
   const int NST = R.nst;
   const int SB = R.stage_blocks;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + NSTMAX;
-  TF* ring = reinterpret_cast<TF*>(smem + 128);
-  TF* w = ring + (size_t)NST * SB * STR;
+  const int nwarps = blockDim.x >> 5;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);                     // [nwarps][NSTMAX]
+  TF* rings = reinterpret_cast<TF*>(smem + 128 * ((nwarps * NSTMAX * 8 + 127) / 128));
+  TF* ring = rings + (size_t)wi * NST * SB * STR;
+  TF* w = rings + (size_t)nwarps * NST * SB * STR;
+  unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 7 * (size_t)R.max_rows);
+  unsigned short* Ucnt = Lcnt + R.max_rows;
+  uint64_t* full = bars + wi * NSTMAX;
   const int s = blockIdx.x;
   const int64_t r0 = R.sd_row[s];
   const int m = (int)(R.sd_row[s + 1] - r0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-row block counts of both streams, next to the vector
-  unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 7 * (size_t)R.max_rows);
-  unsigned short* Ucnt = Lcnt + R.max_rows;
-  const int64_t Lb0 = R.L_off[s], Ub0 = R.U_off[s];
-  const int64_t nLb = R.L_off[s + 1] - Lb0, nUb = R.U_off[s + 1] - Ub0;
-  const int nGL = (int)((nLb + SB - 1) / SB);
-  const int ngroups = nGL + (int)((nUb + SB - 1) / SB);
+  const int D = R.sd_depth[s];
+  const int32_t* ib = R.item_blk + 4 * R.sd_item[s];        // per item: L begin, L end, U begin, U end
+  const int64_t* irow = R.item_row + R.sd_item[s];          // per item: end row
+  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack) + (size_t)R.L_off[s] * STR;
+  const TF* Upack = reinterpret_cast<const TF*>(R.Upack) + (size_t)R.U_off[s] * STR;
 
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NST; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  if (lane == 0)
+    for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   // restriction R_i^delta r into shared memory
   for (int q = threadIdx.x; q < m; q += blockDim.x) {
     const double* src = rin + 7 * (int64_t)R.gnode[r0 + q];
@@ -164,143 +218,148 @@ __global__ void __launch_bounds__(64) k_ras_apply_stream(RasStreamDev R, const d
   }
   __syncthreads();
 
-  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack) + (size_t)Lb0 * STR;
-  const TF* Upack = reinterpret_cast<const TF*>(R.Upack) + (size_t)Ub0 * STR;
+  WarpFeed f{D, wi, 0, 0, 0, 0};
+  const bool active = wi < (1 << D);
+  if (active && lane == 0 && !R.stall)
+    for (int k = 0; k < NST; ++k) feed_issue<TF, STR>(f, R, ib, Lpack, Upack, ring, full, NST, SB);
+  f.issued = __shfl_sync(0xffffffffu, f.issued, 0);
 
-  if (warp == 1) {
-    if (lane == 0) {
-      bool ok = true;
-      int it = 0;
-      for (; it < ngroups && !R.stall; ++it) {
-        const int st = it % NST;
-        if (it >= NST) ok = mbar_wait(&empty[st], ((it / NST) - 1) & 1);
-        if (!ok) break;
-        const bool isL = it < nGL;
-        const int64_t first = (int64_t)(isL ? it : it - nGL) * SB;
-        const int64_t nb = (isL ? nLb : nUb) - first;
-        const uint32_t bytes = (uint32_t)((nb < SB ? nb : SB) * STR * sizeof(TF));
-        mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(ring + (size_t)st * SB * STR, (isL ? Lpack : Upack) + (size_t)first * STR, bytes, &full[st]);
-      }
-      if (!ok) atomicExch(err, 2);
-      // drain: the last copy issued into each stage must land before the CTA
-      // may exit (bounded; on the normal path these phases completed already)
-      for (int k = (it > NST ? it - NST : 0); k < it; ++k) mbar_wait(&full[k % NST], (k / NST) & 1);
-    }
-    return;
-  }
-
-  // consumer warp. Per stage: finish the row that straddles in from the previous
-  // stage, then the rows that lie wholly inside the stage (the common case, no
-  // bookkeeping), then start the row that straddles out; its partial sum carries.
   const int j = lane / 7, c = lane - 7 * (lane / 7);  // block slot 0..3 (4 = idle), component
   bool ok = true;
-  int it = 0;
-  // forward: w_q -= sum_k L_qk w_k
-  {
-    int q = 0, rem = 0;
-    TF acc = TF(0);
-    for (int g = 0; g < nGL; ++g, ++it) {
-      const int st = it % NST;
-      ok = mbar_wait(&full[st], (it / NST) & 1);
-      if (!ok) break;
-      const TF* stg = ring + (size_t)st * SB * STR;
-      const int cap = (int)min((int64_t)SB, nLb - (int64_t)g * SB);
-      int pos = 0;
-      if (rem > 0) {
-        const int k = min(rem, cap);
-        acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
-        pos = k;
-        rem -= k;
+  // wait for the next stage of this warp's sequence; false on timeout
+  auto next_stage = [&]() -> const TF* {
+    const int st = f.used % NST;
+    if (!mbar_wait(&full[st], (f.used / NST) & 1)) return nullptr;
+    return ring + (size_t)st * SB * STR;
+  };
+  // the stage is consumed: lane 0 refills its slot with the next stage in line
+  auto release = [&]() {
+    __syncwarp();
+    f.used++;
+    if (lane == 0 && !R.stall) feed_issue<TF, STR>(f, R, ib, Lpack, Upack, ring, full, NST, SB);
+    f.issued = __shfl_sync(0xffffffffu, f.issued, 0);
+  };
+
+  // forward: phases 0..D, w_q -= sum_k L_qk w_k over the rows of the warp's item
+  for (int p = 0; p <= D; ++p) {
+    const int it = seg_item(D, wi, p);
+    if (it >= 0 && ok) {
+      int q = it == 0 ? 0 : (int)irow[it - 1];
+      const int qe = (int)irow[it];
+      const int nLb = ib[4 * it + 1] - ib[4 * it];
+      int rem = 0, done = 0;
+      TF acc = TF(0);
+      while (done < nLb) {
+        const TF* stg = next_stage();
+        if (!stg) { ok = false; break; }
+        const int cap = min(SB, nLb - done);
+        int pos = 0;
+        if (rem > 0) {
+          const int k = min(rem, cap);
+          acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+          pos = k;
+          rem -= k;
+          if (rem == 0) {
+            if (lane < 7) w[7 * q + lane] -= acc;
+            __syncwarp();
+            ++q;
+          }
+        }
         if (rem == 0) {
-          if (lane < 7) w[7 * q + lane] -= acc;
-          __syncwarp();
-          ++q;
+          for (; q < qe; ++q) {
+            const int nb = Lcnt[q];
+            if (pos + nb > cap) break;
+            const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
+            if (lane < 7 && nb > 0) w[7 * q + lane] -= a;
+            __syncwarp();
+            pos += nb;
+          }
+          if (q < qe && pos < cap) {
+            acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
+            rem = Lcnt[q] - (cap - pos);
+          }
         }
+        done += cap;
+        release();
       }
-      if (rem == 0) {
-        for (; q < m; ++q) {
-          const int nb = Lcnt[q];
-          if (pos + nb > cap) break;
-          const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
-          if (lane < 7 && nb > 0) w[7 * q + lane] -= a;
-          __syncwarp();
-          pos += nb;
-        }
-        if (q < m && pos < cap) {
-          acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
-          rem = Lcnt[q] - (cap - pos);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);
     }
+    __syncthreads();
   }
-  // backward: w_q = D_q^{-1} (w_q - sum_j U_qj w_j); the pivot is the row's first block
-  if (ok) {
-    int q = m - 1, rem = 0;
-    TF acc = TF(0);
-    TF dreg[7];
-    auto finish = [&](int row, TF sum) {
-      const TF t = (lane < 7) ? w[7 * row + lane] - sum : TF(0);
-      TF tv[7];
+  // backward: phases D..0, w_q = D_q^{-1} (w_q - sum_j U_qj w_j), pivot first in each row
+  for (int p = D; p >= 0; --p) {
+    const int it = seg_item(D, wi, 2 * D + 1 - p);
+    if (it >= 0 && ok) {
+      const int qb = it == 0 ? 0 : (int)irow[it - 1];
+      int q = (int)irow[it] - 1;
+      const int nUb = ib[4 * it + 3] - ib[4 * it + 2];
+      int rem = 0, done = 0;
+      TF acc = TF(0);
+      TF dreg[7];
+      auto finish = [&](int row, TF sum) {
+        const TF t = (lane < 7) ? w[7 * row + lane] - sum : TF(0);
+        TF tv[7];
 #pragma unroll
-      for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
-      if (lane < 7) {
-        TF zz = TF(0);
+        for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
+        if (lane < 7) {
+          TF zz = TF(0);
 #pragma unroll
-        for (int mm = 0; mm < 7; ++mm) zz += dreg[mm] * tv[mm];
-        w[7 * row + lane] = zz;
-      }
-      __syncwarp();
-    };
-    auto load_pivot = [&](const TF* blk) {
+          for (int mm = 0; mm < 7; ++mm) zz += dreg[mm] * tv[mm];
+          w[7 * row + lane] = zz;
+        }
+        __syncwarp();
+      };
+      auto load_pivot = [&](const TF* blk) {
 #pragma unroll
-      for (int mm = 0; mm < 7; ++mm) dreg[mm] = lane < 7 ? blk[7 * lane + mm] : TF(0);
-    };
-    for (; it < ngroups; ++it) {
-      const int st = it % NST;
-      ok = mbar_wait(&full[st], (it / NST) & 1);
-      if (!ok) break;
-      const TF* stg = ring + (size_t)st * SB * STR;
-      const int cap = (int)min((int64_t)SB, nUb - (int64_t)(it - nGL) * SB);
-      int pos = 0;
-      if (rem > 0) {
-        const int k = min(rem, cap);
-        acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
-        pos = k;
-        rem -= k;
+        for (int mm = 0; mm < 7; ++mm) dreg[mm] = lane < 7 ? blk[7 * lane + mm] : TF(0);
+      };
+      while (done < nUb) {
+        const TF* stg = next_stage();
+        if (!stg) { ok = false; break; }
+        const int cap = min(SB, nUb - done);
+        int pos = 0;
+        if (rem > 0) {
+          const int k = min(rem, cap);
+          acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+          pos = k;
+          rem -= k;
+          if (rem == 0) {
+            finish(q, acc);
+            --q;
+          }
+        }
         if (rem == 0) {
-          finish(q, acc);
-          --q;
+          for (; q >= qb; --q) {
+            const int nb = Ucnt[q];
+            if (pos + nb > cap) break;
+            const TF* rs = stg + (size_t)pos * STR;
+            load_pivot(rs);
+            finish(q, row_dot<TF, STR>(rs, 1, nb, w, j, c));
+            pos += nb;
+          }
+          if (q >= qb && pos < cap) {
+            const TF* rs = stg + (size_t)pos * STR;
+            load_pivot(rs);
+            acc = row_dot<TF, STR>(rs, 1, cap - pos, w, j, c);
+            rem = Ucnt[q] - (cap - pos);
+          }
         }
+        done += cap;
+        release();
       }
-      if (rem == 0) {
-        for (; q >= 0; --q) {
-          const int nb = Ucnt[q];
-          if (pos + nb > cap) break;
-          const TF* rs = stg + (size_t)pos * STR;
-          load_pivot(rs);
-          finish(q, row_dot<TF, STR>(rs, 1, nb, w, j, c));
-          pos += nb;
-        }
-        if (q >= 0 && pos < cap) {
-          const TF* rs = stg + (size_t)pos * STR;
-          load_pivot(rs);
-          acc = row_dot<TF, STR>(rs, 1, cap - pos, w, j, c);
-          rem = Ucnt[q] - (cap - pos);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);
     }
+    __syncthreads();
   }
   if (!ok) {
-    if (lane == 0) atomicExch(err, 2);
-    return;
+    // a wait gave up: record it and let this warp's copies still in flight land
+    // (bounded) before the CTA exits
+    if (lane == 0) {
+      atomicExch(err, 2);
+      for (int k = f.used; k < f.issued; ++k) mbar_wait(&full[k % NST], (k / NST) & 1);
+    }
   }
-  // restricted prolongation (R_i^0)^T: owned rows only, one row per lane
-  for (int q = lane; q < m; q += 32) {
+  __syncthreads();
+  // restricted prolongation (R_i^0)^T: owned rows only
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
     if (R.owned[r0 + q]) {
       const int64_t g7 = 7 * (int64_t)R.gnode[r0 + q];
 #pragma unroll
@@ -344,8 +403,9 @@ __global__ void k_pack_factors(int64_t nL, const int64_t* __restrict__ Lsrc, con
 
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r) {
-  return 128 + (size_t)r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) + (size_t)7 * r.max_rows * sizeof(TF) +
-         (size_t)4 * r.max_rows + 16;
+  const size_t W = (size_t)1 << r.max_depth;
+  return 128 * ((W * NSTMAX * 8 + 127) / 128) + W * r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) +
+         (size_t)7 * r.max_rows * sizeof(TF) + (size_t)4 * r.max_rows + 16;
 }
 
 template <class TF>
@@ -370,7 +430,7 @@ cudaError_t ras_stream_init(const RasStreamDev& r) {
 template <class TF>
 cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, float* z32, int32_t* err,
                                     const int* guard, cudaStream_t s) {
-  k_ras_apply_stream<TF><<<r.np, 64, ras_stream_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
+  k_ras_apply_stream<TF><<<r.np, 32 << r.max_depth, ras_stream_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,7 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
     L.sd_lvlU.assign(1, 0);
     L.lvlL_ptr.assign(1, 0);
     L.lvlU_ptr.assign(1, 0);
+    L.sd_item.assign(1, 0);
   };
   std::vector<RasPlan> subs(np);
 #pragma omp parallel
@@ -174,56 +175,58 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
     }
     const int64_t m = (int64_t)nodes.size();
     // 3. order of the overlapped subdomain: natural (global node order), reverse
-    //    Cuthill-McKee, or reverse Cuthill-McKee with lumen nodes before wall nodes
+    //    Cuthill-McKee, reverse Cuthill-McKee with lumen nodes before wall nodes,
+    //    or nested dissection with reverse Cuthill-McKee inside each part
     for (int64_t q = 0; q < m; ++q) loc[nodes[q]] = (int32_t)q;
     std::vector<int32_t> order;
     order.reserve(m);
-    if (ordering == 0) {
-      for (int64_t q = 0; q < m; ++q) order.push_back((int32_t)q);
-      std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return nodes[a] < nodes[b]; });
-    } else {
-      std::vector<int32_t> degl(m, 0);
-      for (int64_t q = 0; q < m; ++q) {
-        int32_t v = nodes[q];
-        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e)
-          if (loc[P.col[e]] >= 0 && P.col[e] != v) degl[q]++;
+    // reverse Cuthill-McKee of the local nodes `mem` (the subgraph they induce:
+    // part[w] == pid), appended to `order`: start at the unvisited node of least
+    // degree (ties: lowest node number), move it to the last node a breadth-first
+    // sweep reaches (neighbours in increasing node number), then number breadth
+    // first with each node's new neighbours by (degree, node number); reversed
+    std::vector<int32_t> part(m, 0), degl(m, 0);
+    std::vector<uint8_t> seen(m, 0), s2(m, 0);
+    auto rcm_part = [&](const std::vector<int32_t>& mem, int32_t pid) {
+      for (int32_t q : mem) {
+        int32_t v = nodes[q], d = 0;
+        for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+          const int32_t w = loc[P.col[e]];
+          if (w >= 0 && part[w] == pid && w != q) d++;
+        }
+        degl[q] = d;
+        seen[q] = 0;
       }
-      std::vector<uint8_t> seen(m, 0);
-      std::vector<int32_t> nb;
-      while ((int64_t)order.size() < m) {
-        // start from an unvisited node of minimum degree (a pseudo-peripheral choice)
+      const size_t base = order.size();
+      std::vector<int32_t> nb, bfs;
+      size_t done = 0;
+      while (done < mem.size()) {
         int32_t st = -1;
-        for (int64_t q = 0; q < m; ++q)
-          if (!seen[q] && (st < 0 || degl[q] < degl[st])) st = (int32_t)q;
-        // one BFS sweep to move the start to the far end of the component
-        {
-          std::vector<int32_t> bfs{st};
-          std::vector<uint8_t> s2(m, 0);
-          s2[st] = 1;
-          for (size_t h = 0; h < bfs.size(); ++h) {
-            int32_t v = nodes[bfs[h]];
-            for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
-              int32_t w = loc[P.col[e]];
-              if (w >= 0 && !s2[w] && !seen[w]) {
-                s2[w] = 1;
-                bfs.push_back(w);
-              }
+        for (int32_t q : mem)
+          if (!seen[q] && (st < 0 || degl[q] < degl[st] || (degl[q] == degl[st] && nodes[q] < nodes[st]))) st = q;
+        bfs.assign(1, st);
+        s2[st] = 1;
+        for (size_t h = 0; h < bfs.size(); ++h) {
+          int32_t v = nodes[bfs[h]];
+          for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
+            int32_t w = loc[P.col[e]];
+            if (w >= 0 && part[w] == pid && !s2[w] && !seen[w]) {
+              s2[w] = 1;
+              bfs.push_back(w);
             }
           }
-          int32_t best = bfs.back();
-          // among the last BFS level pick the minimum degree node
-          st = best;
         }
+        for (int32_t q : bfs) s2[q] = 0;
+        st = bfs.back();
         seen[st] = 1;
         size_t head = order.size();
         order.push_back(st);
         while (head < order.size()) {
-          int32_t q = order[head++];
-          int32_t v = nodes[q];
+          int32_t v = nodes[order[head++]];
           nb.clear();
           for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1]; ++e) {
             int32_t w = loc[P.col[e]];
-            if (w >= 0 && !seen[w]) {
+            if (w >= 0 && part[w] == pid && !seen[w]) {
               seen[w] = 1;
               nb.push_back(w);
             }
@@ -233,13 +236,86 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
           });
           order.insert(order.end(), nb.begin(), nb.end());
         }
+        done = order.size() - base;
       }
-      std::reverse(order.begin(), order.end());
+      std::reverse(order.begin() + base, order.end());
+    };
+    int32_t depth = 0;
+    std::vector<int64_t> items{0};  // item row offsets (phase-major)
+    if (ordering == 0) {
+      for (int64_t q = 0; q < m; ++q) order.push_back((int32_t)q);
+      std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return nodes[a] < nodes[b]; });
+    } else if (ordering == 3) {
+      // nested dissection of depth D (the largest D <= 3 with m / 2^D >= 48):
+      // each piece is cut at the median of its longest coordinate axis (order
+      // (coordinate, node number), lower half floor(n/2) nodes); the separator
+      // is the lower half's nodes with a neighbour in the upper half. Items in
+      // phase-major order: the 2^D leaves, then the separators from the deepest
+      // level up to the root's; nodes within an item in reverse Cuthill-McKee order
+      while (depth < 3 && m >= ((int64_t)ND_MIN_LEAF << (depth + 1))) ++depth;
+      std::vector<std::vector<int32_t>> cur(1), next;
+      for (int64_t q = 0; q < m; ++q) cur[0].push_back((int32_t)q);
+      std::vector<std::vector<std::vector<int32_t>>> seps(depth);
+      for (int32_t d = 0; d < depth; ++d) {
+        next.clear();
+        for (auto& S : cur) {
+          double bmin[3] = {1e300, 1e300, 1e300}, bmax[3] = {-1e300, -1e300, -1e300};
+          for (int32_t q : S)
+            for (int c = 0; c < 3; ++c) {
+              bmin[c] = std::min(bmin[c], X[3 * (int64_t)nodes[q] + c]);
+              bmax[c] = std::max(bmax[c], X[3 * (int64_t)nodes[q] + c]);
+            }
+          int ax = 0;
+          for (int c = 1; c < 3; ++c)
+            if (bmax[c] - bmin[c] > bmax[ax] - bmin[ax]) ax = c;
+          std::sort(S.begin(), S.end(), [&](int32_t a, int32_t b) {
+            const double xa = X[3 * (int64_t)nodes[a] + ax], xb = X[3 * (int64_t)nodes[b] + ax];
+            return xa < xb || (xa == xb && nodes[a] < nodes[b]);
+          });
+          const size_t half = S.size() / 2;
+          for (size_t k = 0; k < S.size(); ++k) part[S[k]] = k < half ? 1 : 2;
+          std::vector<int32_t> A, B(S.begin() + half, S.end()), sep;
+          for (size_t k = 0; k < half; ++k) {
+            const int32_t q = S[k], v = nodes[q];
+            bool cut = false;
+            for (int64_t e = P.row_ptr[v]; e < P.row_ptr[v + 1] && !cut; ++e) {
+              const int32_t w = loc[P.col[e]];
+              cut = w >= 0 && part[w] == 2;
+            }
+            (cut ? sep : A).push_back(q);
+          }
+          for (int32_t q : S) part[q] = 0;
+          next.push_back(std::move(A));
+          next.push_back(std::move(B));
+          seps[d].push_back(std::move(sep));
+        }
+        cur.swap(next);
+      }
+      // phase-major items, each ordered by RCM on the subgraph it induces
+      std::vector<std::vector<int32_t>*> it;
+      for (auto& S : cur) it.push_back(&S);
+      for (int32_t d = depth - 1; d >= 0; --d)
+        for (auto& S : seps[d]) it.push_back(&S);
+      for (size_t k = 0; k < it.size(); ++k)
+        for (int32_t q : *it[k]) part[q] = (int32_t)k + 1;
+      for (size_t k = 0; k < it.size(); ++k) {
+        rcm_part(*it[k], (int32_t)k + 1);
+        items.push_back((int64_t)order.size());
+      }
+      for (int64_t q = 0; q < m; ++q) part[q] = 0;
+    } else {
+      std::vector<int32_t> all(m);
+      for (int64_t q = 0; q < m; ++q) all[q] = (int32_t)q;
+      rcm_part(all, 0);
       if (ordering == 2 && node_rank) {
         std::stable_sort(order.begin(), order.end(),
                          [&](int32_t a, int32_t b) { return node_rank[nodes[a]] < node_rank[nodes[b]]; });
       }
     }
+    if (items.size() == 1) items.push_back(m);
+    R.sd_depth.push_back(depth);
+    for (size_t k = 1; k < items.size(); ++k) R.item_row.push_back(items[k]);
+    R.sd_item.push_back((int64_t)R.item_row.size());
     std::vector<int32_t> perm(m);  // old local -> new local
     for (int64_t q = 0; q < m; ++q) perm[order[q]] = (int32_t)q;
     std::vector<int32_t> gn(m);
@@ -376,9 +452,11 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
   // the subdomains before them (sizes and offsets first, then the copies in
   // parallel, one subdomain per task)
   std::vector<int64_t> oR(np + 1, 0), oB(np + 1, 0), oL(np + 1, 0), oU(np + 1, 0);
-  std::vector<int64_t> oLR(np + 1, 0), oUR(np + 1, 0), oLP(np + 1, 0), oUP(np + 1, 0);
+  std::vector<int64_t> oLR(np + 1, 0), oUR(np + 1, 0), oLP(np + 1, 0), oUP(np + 1, 0), oI(np + 1, 0);
   for (int32_t s = 0; s < np; ++s) {
     const RasPlan& L = subs[s];
+    oI[s + 1] = oI[s] + (int64_t)L.item_row.size();
+    R.max_depth = std::max(R.max_depth, L.sd_depth.empty() ? 0 : L.sd_depth[0]);
     oR[s + 1] = oR[s] + (int64_t)L.gnode.size();
     oB[s + 1] = oB[s] + (int64_t)L.col.size();
     oL[s + 1] = oL[s] + (int64_t)L.lent_pos.size();
@@ -407,6 +485,9 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
   R.lvlL_ptr.assign(oLP[np] + 1, 0);
   R.lvlU_ptr.assign(oUP[np] + 1, 0);
   R.sd_row.assign(oR.begin(), oR.end());
+  R.sd_item.assign(oI.begin(), oI.end());
+  R.item_row.resize(oI[np]);
+  R.sd_depth.resize(np);
   R.sd_lvlL.assign(oLP.begin(), oLP.end());
   R.sd_lvlU.assign(oUP.begin(), oUP.end());
 #pragma omp parallel for schedule(dynamic, 4)
@@ -434,6 +515,8 @@ RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n, const int32_t
       R.upd_tgt[UO + u] = L.upd_tgt[u] + BO;
       R.upd_src[UO + u] = L.upd_src[u] + BO;
     }
+    std::copy(L.item_row.begin(), L.item_row.end(), R.item_row.begin() + oI[s]);
+    R.sd_depth[s] = L.sd_depth[0];
     std::copy(L.lvlL_rows.begin(), L.lvlL_rows.end(), R.lvlL_rows.begin() + oLR[s]);
     std::copy(L.lvlU_rows.begin(), L.lvlU_rows.end(), R.lvlU_rows.begin() + oUR[s]);
     for (size_t i = 1; i < L.lvlL_ptr.size(); ++i) R.lvlL_ptr[oLP[s] + i] = L.lvlL_ptr[i] + oLR[s];

@@ -64,12 +64,26 @@ struct RasPlan {
   std::vector<int32_t> lvlL_rows, lvlU_rows; // concatenated local rows (subdomain-relative)
   int32_t max_levels = 0;
   int64_t max_rows = 0;
+  // nested-dissection items of each subdomain (one item, depth 0, for the
+  // other orderings): 2^(D+1) - 1 items in phase-major order (the 2^D leaves,
+  // then the separators from the deepest level up to the root's); item k of
+  // subdomain s ends at local row item_row[sd_item[s] + k] (item 0 starts at 0)
+  std::vector<int32_t> sd_depth;   // [np] D
+  std::vector<int64_t> sd_item;    // [np+1]
+  std::vector<int64_t> item_row;   // [sum of items]
+  int32_t max_depth = 0;
 };
+
+// smallest average leaf of the nested-dissection ordering: the depth D of a
+// subdomain of m rows is the largest D <= 3 with m >= ND_MIN_LEAF * 2^D
+constexpr int32_t ND_MIN_LEAF = 48;
 
 // fill_level k: pattern of the level-of-fill ILU(k) of each J_i^delta (0 = the
 // pattern of J_i^delta itself). ordering of each subdomain: 0 natural (global
 // node order), 1 reverse Cuthill-McKee, 2 reverse Cuthill-McKee stably sorted
-// by node_rank (lumen nodes 0, interface 1, wall 2).
+// by node_rank (lumen nodes 0, interface 1, wall 2), 3 nested dissection
+// (coordinate bisection, one-sided vertex separators) with reverse
+// Cuthill-McKee inside every part.
 RasPlan build_ras(const BsrPattern& P, const double* X, int64_t n_nodes, const int32_t* node_problem,
                   int32_t n_problems, int32_t np, int32_t overlap, int32_t fill_level, int32_t ordering,
                   const uint8_t* node_rank);

@@ -49,7 +49,8 @@ class FsiOptions(ctypes.Structure):
                 ("n_subdomains", ctypes.c_int32), ("overlap", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("jac_lag", ctypes.c_int32), ("ilu_level", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
                 ("ordering", ctypes.c_int32), ("factor_mode", ctypes.c_int32),
-                ("verbose", ctypes.c_int32), ("fault_test", ctypes.c_int32)]
+                ("verbose", ctypes.c_int32), ("fault_test", ctypes.c_int32), ("apply_mode", ctypes.c_int32),
+                ("stage_blocks", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
 class FsiSolveStats(ctypes.Structure):
@@ -72,7 +73,8 @@ class FsiInfo(ctypes.Structure):
                 ("nnzb", ctypes.c_int64), ("n_fluid_tets", ctypes.c_int64), ("n_wall_tets", ctypes.c_int64),
                 ("n_problems", ctypes.c_int32), ("n_subdomains", ctypes.c_int32),
                 ("factor_blocks", ctypes.c_int64), ("factor_rows", ctypes.c_int64), ("max_levels", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64), ("n_wss_faces", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("n_wss_faces", ctypes.c_int64), ("nd_depth", ctypes.c_int32),
+                ("apply_kernel", ctypes.c_int32)]
 
 
 def load_library(path=LIB_PATH):

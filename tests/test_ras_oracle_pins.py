@@ -228,3 +228,47 @@ def test_full_fill_on_the_fsi_jacobian_is_exact():
     z = RO.RAS(J, m.X, m.tets, None, 1, 1, 1, 20, 1).apply(r)
     res = r.reshape(-1) - J @ z.reshape(-1)
     assert np.linalg.norm(res) < 1e-8 * np.linalg.norm(r)
+
+
+def test_nested_dissection_items_are_independent():
+    """Nested dissection (Sec. 4.5): the items cover the subdomain once, and no
+    edge and no fill entry of any level (even full fill) joins two items of the
+    same phase, so their triangular solves can run side by side; D follows the
+    leaf-size rule."""
+    m = vm.tube_mesh(8, 12, 3, 1, seed=4)
+    n = m.n_nodes
+    adj = RO.node_graph(n, m.tets)
+    nodes = np.arange(n)
+    items, D = RO.nested_dissection(nodes, adj, m.X)
+    assert D == 3 and len(items) == 2 ** (D + 1) - 1
+    assert sorted(v for it in items for v in it) == list(range(n))
+    order = RO.subdomain_order(nodes, adj, 3, X=m.X)
+    pos = np.empty(n, dtype=int)
+    pos[order] = np.arange(n)
+    lev = RO.ilu_levels(order, adj, n)                  # every fill entry kept
+    phases, k = [], 0
+    for p in range(D + 1):
+        cnt = 2 ** (D - p)
+        phases.append(items[k:k + cnt])
+        k += cnt
+    for ph in phases:
+        for a in range(len(ph)):
+            for b in range(len(ph)):
+                if a == b or not ph[a] or not ph[b]:
+                    continue
+                ia, ib = pos[np.array(ph[a])], pos[np.array(ph[b])]
+                assert (lev[np.ix_(ia, ib)] <= n).sum() == 0
+    # a small subdomain is not dissected
+    assert RO.nested_dissection(nodes[:95], adj, m.X)[1] == 0
+    assert RO.nested_dissection(nodes[:96], adj, m.X)[1] == 1
+
+
+def test_nested_dissection_full_fill_is_exact():
+    m = vm.tube_mesh(3, 8, 2, 1, seed=5)
+    n = m.n_nodes
+    adj = RO.node_graph(n, m.tets)
+    J = block_matrix_on_graph(adj, 15, diag_shift=2.0)
+    r = np.random.default_rng(16).normal(size=(n, 7))
+    z = RO.RAS(J, m.X, m.tets, None, 1, 1, 0, n, 3).apply(r)
+    ze = exact(J, r)
+    assert np.abs(z - ze).max() < 1e-11 * np.abs(ze).max()
