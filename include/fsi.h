@@ -192,12 +192,16 @@ typedef struct {
  * caller's options also selects the default. */
 void fsi_default_options(fsi_options *opts);
 
-/* Build a solver context for `mesh`. bc: array of n_problems inflow boundaries
- * (n_problems >= 1; node_problem picks one per node). Performs all symbolic
- * work on the host (block-sparse pattern, assembly gather lists, subdomain
- * partition, overlap, RCM ordering, ILU pattern, level schedules), copies the
- * mesh to the device and allocates every device buffer the solver needs. The
- * state is zero until fsi_set_state. `cuda_stream` is a cudaStream_t.
+/* Build a solver context for `mesh` (the discrete problem of Sec. 2.2, Eq. 6-7:
+ * one block of 7 unknowns per mesh node, strong coupling at the interface
+ * nodes; its Schwarz subdomains Omega_i and overlaps Omega_i^delta of Sec. 3,
+ * Eq. 14). bc: array of n_problems inflow boundaries (n_problems >= 1;
+ * node_problem picks one per node). Performs all symbolic work on the host
+ * (block-sparse pattern, assembly gather lists, subdomain partition, overlap,
+ * subdomain ordering, ILU(k) pattern, level schedules), copies the mesh to the
+ * device and allocates every device buffer the solver needs. The state is zero
+ * until fsi_set_state. `cuda_stream` is a cudaStream_t. Host pointers inside
+ * mesh / mat / bc are read during the call only.
  * Errors: FSI_ERR_ARG, FSI_ERR_MESH, FSI_ERR_NOMEM, FSI_ERR_CUDA; *out is NULL
  * on failure. */
 fsi_status fsi_create(const fsi_mesh *mesh, const fsi_material *mat, const fsi_bc *bc,
@@ -224,7 +228,10 @@ fsi_status fsi_residual(fsi_ctx *ctx, const double *y, double *F);
 
 /* Assemble the exact Jacobian J = dF/dy at y (device, [n_nodes*7]) into the
  * context's block-sparse (7x7 BSR) matrix, in FP64 or, in mixed precision, in
- * FP32. Marks the preconditioner stale; it is rebuilt by the next linear solve. */
+ * FP32: the Jacobian of Eq. 12 formed analytically (exact derivatives of every
+ * term, stabilisation parameters included; Sec. 3). The matrix is owned by the
+ * context. Marks the preconditioner stale; it is rebuilt by the next linear
+ * solve. Errors: FSI_ERR_ARG (null pointer), FSI_ERR_CUDA. */
 fsi_status fsi_jacobian(fsi_ctx *ctx, const double *y);
 
 /* Copy the assembled Jacobian out. Host pointers, any may be NULL:
@@ -239,16 +246,26 @@ fsi_status fsi_spmv(fsi_ctx *ctx, const double *x, double *y);
  * from the assembled Jacobian (built first if stale). Device pointers, FP64. */
 fsi_status fsi_pc_apply(fsi_ctx *ctx, const double *r, double *z);
 
-/* Solve J x = rhs with right-preconditioned restarted GMRES to the context's
- * gmres_rtol on the true residual. Device pointers, [n_nodes*7]; x is the
- * output (initial guess 0). stats may be NULL. Returns
- * FSI_ERR_LINEAR_DIVERGED (x still holds the last iterate) if gmres_maxit is
- * reached. */
+/* Solve J x = rhs, the Newton correction system of Eq. 12-13, with
+ * right-preconditioned restarted (flexible) GMRES and the restricted additive
+ * Schwarz preconditioner of Eq. 14-16 (built first if stale), to the context's
+ * gmres_rtol on the true residual. Device pointers, [n_nodes*7]; rhs is read,
+ * x is the output (initial guess 0). stats (host, may be NULL) gets the
+ * iteration count and residual norms. Returns FSI_ERR_LINEAR_DIVERGED (x still
+ * holds the last iterate) if gmres_maxit is reached; FSI_ERR_ARG if no Jacobian
+ * was assembled; FSI_ERR_ZERO_PIVOT if a subdomain factor has a singular pivot
+ * block; FSI_ERR_TIMEOUT if a bounded device wait gave up. */
 fsi_status fsi_linear_solve(fsi_ctx *ctx, const double *rhs, double *x, fsi_solve_stats *stats);
 
-/* One backward-Euler step: Newton from y^(0) = y_n to the Newton tolerance,
- * then shift the time levels (y_{n-2} <- y_{n-1} <- y_n <- y, t <- t + dt). On
- * failure the state is left at the previous time level. stats may be NULL. */
+/* One backward-Euler step (Eq. 9-10: the fully implicit system F(y) = 0 at
+ * t_n + dt): inexact Newton with backtracking from y^(0) = y_n (Sec. 3, Eq.
+ * 11-12; the Jacobian is rebuilt every jac_lag iterations), each correction from
+ * fsi_linear_solve's GMRES, to the Newton tolerance; then the time levels shift
+ * (y_{n-2} <- y_{n-1} <- y_n <- y, t <- t + dt). stats (host, may be NULL) gets
+ * the iteration counts and, when given, per-phase device times. Errors:
+ * FSI_ERR_DIVERGED (newton_maxit reached), FSI_ERR_LINESEARCH,
+ * FSI_ERR_NONFINITE, FSI_ERR_ZERO_PIVOT, FSI_ERR_TIMEOUT, FSI_ERR_CUDA; on any
+ * failure the state is left at the previous time level. */
 fsi_status fsi_step(fsi_ctx *ctx, fsi_step_stats *stats);
 
 /* Wall shear stress on the inner wall of every problem (the WSS and SAWSS
@@ -275,14 +292,18 @@ fsi_status fsi_get_info(const fsi_ctx *ctx, fsi_info *info);
  * allocate device memory, e.g. code that fixed its device-memory footprint in
  * advance or that runs while device allocation is not allowed: it computes the
  * same F(y) as fsi_residual (same arguments, device pointers [n_nodes*7] FP64)
- * and allocates nothing, because its assembly scratch (28 FP64 values per tet)
- * is one fixed device array built into the library, sized for at most 32,768
- * tets (7.3 MB, held by every GPU that loads the library until the process
- * exits). Larger meshes get FSI_ERR_ARG with a message. The first call on a
- * device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture. All calls
- * share the one array: calls that overlap on the GPU (other streams, other
- * contexts, other host threads) race and must be serialised by the caller. */
+ * and allocates nothing itself, because its assembly scratch (28 FP64 values
+ * per tet) is one fixed device array built into the library, sized for at most
+ * 32,768 tets (7.3 MB per device). Larger meshes get FSI_ERR_ARG with a
+ * message. The first call on a device looks up that array's device address
+ * (once per device, with the device current); under CUDA's lazy module loading
+ * that first lookup is also when the driver loads the library's device code and
+ * commits the array's memory on that device, so a caller that must not see any
+ * allocation during its run makes one warm-up call per device beforehand (and
+ * before any stream capture). From then on every GPU that has done so holds the
+ * array until the process exits. All calls share the one array: calls that
+ * overlap on the GPU (other streams, other contexts, other host threads) race
+ * and must be serialised by the caller. */
 fsi_status fsi_residual_noalloc(fsi_ctx *ctx, const double *y, double *F);
 
 /* Message of the last failure on the context (static string if ctx is NULL). */
