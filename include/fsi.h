@@ -128,12 +128,14 @@ typedef struct {
                              before interface and wall nodes, 3 nested dissection
                              (coordinate bisection, up to 3 levels, RCM inside each
                              part; the parts of one level are solved side by side) */
-  int32_t factor_mode;    /* shared-memory use of the ILU factorisation: 0 automatic
-                             (= 3, the fastest measured); 1 pivots and update sources
-                             prefetched into shared memory, 2 sources only, 3 neither
-                             (the row alone in shared memory). A forced mode whose
-                             footprint does not fit is FSI_ERR_ARG. All modes give
-                             bitwise identical factors. */
+  int32_t factor_mode;    /* ILU factorisation kernel: 0 automatic (4 when the
+                             subdomains are dissected, ordering 3, and its rows fit in
+                             shared memory, else 3); rows in order with 1 pivots and
+                             update sources prefetched into shared memory, 2 sources
+                             only, 3 neither (the row alone in shared memory); 4 the
+                             parts of each dissection level factored side by side. A
+                             forced mode whose footprint does not fit is FSI_ERR_ARG.
+                             All modes give bitwise identical factors. */
   int32_t verbose;        /* print per-iteration norms to stderr */
   int32_t fault_test;     /* tests only: 1 = the preconditioner apply's copy engine
                              issues nothing, so the apply's bounded wait runs out and

@@ -528,7 +528,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       if (q.ordering >= 0 && q.ordering <= 3) o.ordering = q.ordering;
       o.verbose = q.verbose;
       o.fault_test = q.fault_test;
-      if (q.factor_mode >= 0 && q.factor_mode <= 3) o.factor_mode = q.factor_mode;
+      if (q.factor_mode >= 0 && q.factor_mode <= 4) o.factor_mode = q.factor_mode;
       o.apply_mode = q.apply_mode;
       o.stage_blocks = q.stage_blocks;
       o.stages = q.stages;
@@ -814,8 +814,14 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rd.max_row_lent = (int32_t)ml;
       rd.max_row_upd = (int32_t)mu;
       rd.max_entry_upd = (int32_t)me;
-      const int want = o.factor_mode > 0 ? o.factor_mode - 1 : 2;
+      rd.sd_depth = cp->upload(R.sd_depth);
+      rd.sd_item = cp->upload(R.sd_item);
+      rd.item_row = cp->upload(R.item_row);
+      rd.max_depth = R.max_depth;
       auto fits = [&](int mode) { return cp->mixed ? ras_factor_fits<float>(rd, mode) : ras_factor_fits<double>(rd, mode); };
+      // automatic: nested-dissection groups when the subdomains are dissected and
+      // the groups' rows fit, else the row-only sequential kernel
+      const int want = o.factor_mode > 0 ? o.factor_mode - 1 : (R.max_depth > 0 && fits(3) ? 3 : 2);
       rd.factor_mode = want;
       if (fits(2) && !fits(want)) throw StatusError{FSI_ERR_ARG, "factor_mode needs more shared memory than fits"};
       if (!fits(2)) {

@@ -81,14 +81,18 @@ struct RasDev {
   int32_t max_row_lent;    // most L blocks in one row
   int32_t max_row_upd;     // most elimination updates in one row
   int32_t max_entry_upd;   // most updates of one L block
-  int32_t factor_mode;     // shared-memory mode of the factorisation CTA (0..2)
+  int32_t factor_mode;     // factorisation kernel: 0..2 rows in order (shared-memory modes), 3 nested-dissection groups
+  const int32_t* sd_depth; // [np] nested-dissection depth of each subdomain (0: one item)
+  const int64_t* sd_item;  // [np+1] first item of each subdomain
+  const int64_t* item_row; // [items] end row of each item (subdomain-relative)
+  int32_t max_depth;       // deepest dissection (the nested-dissection factorisation uses 2^max_depth groups)
 };
 template <class TF, class TJ>
 void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s);
 template <class TF>
 void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s);
 template <class TF>
-bool ras_factor_fits(const RasDev& r, int mode);  // shared-memory mode 0..2 fits one CTA
+bool ras_factor_fits(const RasDev& r, int mode);  // mode 0..3 fits one CTA
 // shared-memory limit of the factorisation CTA (the opt-in maximum)
 constexpr size_t FACTOR_SMEM_MAX = 227 * 1024;
 template <class TF>

@@ -22,8 +22,9 @@ inline int grid_for(int64_t work, int block) {
 // SpMV: one warp per block row. Lane l < 28 owns output component r = l / 4 and
 // every fourth block (q = l % 4) of the row; the four partial sums of a
 // component are combined by two shuffles. Lanes 28..31 idle. FP64: values,
-// vector and sums in FP64. Mixed: FP32 values and an FP32 copy of the vector,
-// sums in FP32, result stored in FP64 (no FP64 arithmetic in the loop).
+// vector and sums in FP64. Mixed: FP32 values and an FP32 copy of the vector;
+// each block's 7-term product is formed in FP32 and the block products are
+// accumulated in FP64 (one FP64 add per block and component), result in FP64.
 // ---------------------------------------------------------------------------
 template <class TV, class TX, int S>
 __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __restrict__ row_ptr,
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __re
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / G;
   for (int64_t base = grp0 - (lane / G); base < n; base += ngrp) {
     const int64_t row = base + (lane / G);
-    TX acc = TX(0);
+    double acc = 0.0;
     if (r < 7 && row < n) {
       const int64_t b0 = row_ptr[row], b1 = row_ptr[row + 1];
       // four of this lane's blocks per pass: their column indices first, then
@@ -57,14 +58,14 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(int64_t n, const int64_t* __re
             TX s0 = TX(A[0]) * xb[0] + TX(A[1]) * xb[1];
             TX s1 = TX(A[2]) * xb[2] + TX(A[3]) * xb[3];
             TX s2 = TX(A[4]) * xb[4] + TX(A[5]) * xb[5];
-            acc += (s0 + s1) + (s2 + TX(A[6]) * xb[6]);
+            acc += (double)((s0 + s1) + (s2 + TX(A[6]) * xb[6]));
           }
         }
       }
     }
 #pragma unroll
     for (int o = 1; o < S; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (r < 7 && q == 0 && row < n) y[7 * row + r] = (double)acc;
+    if (r < 7 && q == 0 && row < n) y[7 * row + r] = acc;
   }
 }
 
@@ -157,7 +158,8 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
 // threads 0..48 form A_ik D_k^{-1} (D_k: the inverted pivot of the finished row
 // k; into a separate buffer and the row), then all threads apply its updates
 // A_ij -= A_ik A_kj (task = update x column) - two barriers per L block.
-// MODE picks how much besides the row lives in shared memory, largest first:
+// MODE picks how much besides the row lives in shared memory, largest first
+// (the factor_mode option of fsi_options is MODE + 1):
 //   0: the pivots D_k of all L blocks of the row, loaded with the row, and the
 //      source blocks A_kj of each L block's updates in a cp.async double
 //      buffer, one L block ahead (their latency hides behind the previous L
@@ -165,7 +167,8 @@ __device__ void warp_invert7(TF* B, TF* aug, int32_t* err) {
 //   1: as 0 but D_k read from global memory (L2) when used;
 //   2: only the row: D_k and the sources read from global memory when used.
 // All three do the same arithmetic in the same order (bitwise identical
-// factors); mode 2 is the default (see ras_factor_fits).
+// factors); MODE 2 (factor_mode 3, the row only) is the default (see
+// ras_factor_fits).
 template <class TF>
 __device__ __forceinline__ void cp_async_elem(TF* dst, const TF* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -254,6 +257,88 @@ __global__ void __launch_bounds__(256) k_ras_factor_cta(RasDev R, TF* __restrict
     if (tid < 32) warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
     __syncthreads();
     for (int idx = tid; idx < 49 * nblk; idx += nt) fac[49 * rp + idx] = sRow[idx];
+    __syncthreads();
+  }
+}
+
+// Block ILU on nested-dissection ordered subdomains: the CTA's 256 threads
+// form G = 2^D groups (D the subdomain's dissection depth); in each phase (the
+// leaves, then the separators level by level) every item of the phase is
+// factored by its own group, row by row exactly as MODE 2 of k_ras_factor_cta
+// does it (the row in shared memory, pivots and sources read from global
+// memory), with the group's own barrier instead of the CTA's. Items of one
+// phase share no entry, so their rows can be eliminated side by side; the
+// arithmetic of every row is that of the sequential kernel, in the same order
+// (bitwise identical factors). A CTA barrier separates the phases.
+__device__ __forceinline__ void group_sync(int g, int gs) {
+  if (gs == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(gs) : "memory");
+  }
+}
+
+template <class TF>
+__global__ void __launch_bounds__(256) k_ras_factor_nd(RasDev R, TF* __restrict__ fac, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int s = blockIdx.x;
+  const int D = R.sd_depth[s];
+  const int G = 1 << D, gs = blockDim.x / G;
+  const int g = threadIdx.x / gs, lt = threadIdx.x - g * gs;
+  const size_t per = (size_t)(R.max_row_blocks + 1) * 49 + 98;
+  TF* sRow = reinterpret_cast<TF*>(fsm) + (size_t)g * per;
+  TF* sScl = sRow + (size_t)R.max_row_blocks * 49;
+  TF* sAug = sScl + 49;
+  const int64_t r0 = R.sd_row[s];
+  const int64_t* irow = R.item_row + R.sd_item[s];
+  for (int p = 0; p <= D; ++p) {
+    const int nit = 1 << (D - p);
+    if (g < nit) {
+      const int it = (1 << (D + 1)) - (1 << (D - p + 1)) + g;
+      const int64_t qb = r0 + (it == 0 ? 0 : irow[it - 1]), qe = r0 + irow[it];
+      for (int64_t q = qb; q < qe; ++q) {
+        const int64_t rp = R.row_ptr[q];
+        const int nblk = (int)(R.row_ptr[q + 1] - rp);
+        const int64_t e0 = R.lent_ptr[q], e1 = R.lent_ptr[q + 1];
+        for (int idx = lt; idx < 49 * nblk; idx += gs) sRow[idx] = fac[49 * rp + idx];
+        group_sync(g, gs);
+        for (int64_t e = e0; e < e1; ++e) {
+          TF* Aik = sRow + 49 * (R.lent_pos[e] - rp);
+          const TF* Dk = fac + 49 * R.lent_kdiag[e];
+          for (int x = lt; x < 49; x += gs) {
+            const int r = x / 7, c = x - 7 * r;
+            TF v = TF(0);
+#pragma unroll
+            for (int mm = 0; mm < 7; ++mm) v += Aik[7 * r + mm] * Dk[7 * mm + c];
+            sScl[x] = v;
+          }
+          group_sync(g, gs);
+          for (int x = lt; x < 49; x += gs) Aik[x] = sScl[x];
+          const int64_t ub = R.upd_ptr[e];
+          const int ntask = 7 * (int)(R.upd_ptr[e + 1] - ub);
+          for (int t = lt; t < ntask; t += gs) {
+            const int u = t / 7, cc = t - 7 * u;
+            TF* Aij = sRow + 49 * (R.upd_tgt[ub + u] - rp) + cc;
+            const TF* Akj = fac + 49 * R.upd_src[ub + u] + cc;
+            TF col[7];
+#pragma unroll
+            for (int mm = 0; mm < 7; ++mm) col[mm] = Akj[7 * mm];
+#pragma unroll
+            for (int rr = 0; rr < 7; ++rr) {
+              TF acc = Aij[7 * rr];
+#pragma unroll
+              for (int mm = 0; mm < 7; ++mm) acc -= sScl[7 * rr + mm] * col[mm];
+              Aij[7 * rr] = acc;
+            }
+          }
+          group_sync(g, gs);
+        }
+        if (lt < 32) warp_invert7<TF>(sRow + 49 * (R.diag[q] - rp), sAug, err);
+        group_sync(g, gs);
+        for (int idx = lt; idx < 49 * nblk; idx += gs) fac[49 * rp + idx] = sRow[idx];
+        group_sync(g, gs);
+      }
+    }
     __syncthreads();
   }
 }
@@ -363,6 +448,8 @@ void launch_ras_extract(const RasDev& r, const TJ* vals, TF* fac, cudaStream_t s
 
 template <class TF>
 size_t ras_factor_cta_smem(const RasDev& r, int mode) {
+  if (mode == 3)  // one row, scaled block and inversion scratch per group
+    return ((size_t)1 << r.max_depth) * (((size_t)r.max_row_blocks + 1) * 49 + 98) * sizeof(TF);
   size_t blocks = (size_t)r.max_row_blocks + 1;  // the row and the scaled L block
   if (mode == 0) blocks += (size_t)r.max_row_lent + 2 * (size_t)r.max_entry_upd;
   if (mode == 1) blocks += 2 * (size_t)r.max_entry_upd;
@@ -393,6 +480,12 @@ void launch_ras_factor(const RasDev& r, TF* fac, int32_t* err, cudaStream_t s) {
     case 0: launch_factor_mode<TF, 0>(r, fac, err, smem, s); break;
     case 1: launch_factor_mode<TF, 1>(r, fac, err, smem, s); break;
     case 2: launch_factor_mode<TF, 2>(r, fac, err, smem, s); break;
+    case 3:
+      cudaFuncSetAttribute(k_ras_factor_nd<TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+      cudaFuncSetAttribute(k_ras_factor_nd<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_ras_factor_nd<TF><<<r.np, 256, smem, s>>>(r, fac, err);
+      break;
     default: break;  // fsi_create rejects such plans
   }
 }

@@ -200,16 +200,18 @@ def test_newton_steps_mixed_match_oracle(tube0, oracle_tube0_steps):
         assert all(v < 1e-6 for v in rel.values()), (k, rel)
 
 
-@pytest.mark.parametrize("precision,ilu", [(0, 1), (1, 2)])
-def test_factor_shared_memory_modes_are_bitwise_identical(tube0, precision, ilu):
-    """The three shared-memory modes of the ILU factorisation (pivots and
-    sources prefetched / sources only / neither) do the same arithmetic in the
-    same order, so the preconditioner applies agree bit for bit."""
+@pytest.mark.parametrize("precision,ilu,ordering", [(0, 1, 1), (1, 2, 1), (0, 2, 3), (1, 1, 3)])
+def test_factor_shared_memory_modes_are_bitwise_identical(tube0, precision, ilu, ordering):
+    """The shared-memory modes of the ILU factorisation (pivots and sources
+    prefetched / sources only / neither) and the nested-dissection grouped
+    kernel (ordering 3) do the same arithmetic in the same order, so the
+    preconditioner applies agree bit for bit."""
     y = vm.poiseuille_state(tube0)
     r = torch.randn((tube0.n_nodes, 7), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
     outs = []
-    for mode in (1, 2, 3):
-        S = make_solver(tube0, precision=precision, ilu_level=ilu, n_subdomains=4, factor_mode=mode)
+    for mode in ((1, 2, 3) if ordering != 3 else (1, 2, 3, 4)):
+        S = make_solver(tube0, precision=precision, ilu_level=ilu, n_subdomains=4 if ordering != 3 else 1,
+                        ordering=ordering, factor_mode=mode)
         S.set_state(y, t=0.0)
         S.jacobian(y)
         z = S.vec()
@@ -217,7 +219,7 @@ def test_factor_shared_memory_modes_are_bitwise_identical(tube0, precision, ilu)
         outs.append(z.cpu().numpy())
         S.close()
     assert np.isfinite(outs[0]).all()
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
 def test_newton_steps_with_jacobian_lag_match_oracle(tube0, oracle_tube0_steps):
