@@ -922,7 +922,9 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
       const int64_t per_sm = std::min<int64_t>(8, (R.np + 151) / 152);
       const int64_t fixed = 128 * ((W * 64 + 127) / 128) + 7 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
-      int64_t SB = ((int64_t)(227 * 1024) / per_sm - fixed) / (W * nst * stride * vsz);
+      // (the budget never exceeds the 200 KB the streamed apply may use)
+      const int64_t budget = std::min<int64_t>((int64_t)(227 * 1024) / per_sm, (int64_t)(200 * 1024));
+      int64_t SB = (budget - fixed) / (W * nst * stride * vsz);
       SB = std::max<int64_t>(W > 1 ? 8 : 16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
       if (o.stage_blocks > 0) SB = o.stage_blocks;
       (void)maxblk;

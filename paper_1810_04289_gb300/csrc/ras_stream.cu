@@ -127,8 +127,8 @@ __device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w
 // arrive while the CTA waits at the phase barrier).
 struct WarpFeed {
   int D, wi;         // nested-dissection depth of the subdomain, warp index
-  int seg;           // producer: current segment 0 .. 2D+1, block offset in it
-  int off;
+  int seg;           // producer: current segment 0 .. 2D+1 (2D+2 = done)
+  int pos, end;      // producer: next block to issue and end block of the current segment
   int issued, used;  // stages issued / consumed by this warp
 };
 
@@ -139,30 +139,35 @@ __device__ __forceinline__ int seg_item(int D, int wi, int j) {
   return (1 << (D + 1)) - (1 << (D - p + 1)) + wi;
 }
 
-template <class TF, int STR>
-__device__ __forceinline__ void feed_issue(WarpFeed& f, const RasStreamDev& R, const int32_t* ib, const TF* Lpack,
-                                           const TF* Upack, TF* ring, uint64_t* full, int NST, int SB) {
-  while (f.seg <= 2 * f.D + 1) {
+// lane 0: move the producer to the first segment at or after f.seg that has
+// blocks left, loading its bounds once (segment changes are rare: 2D + 2 per apply)
+__device__ __forceinline__ void feed_seek(WarpFeed& f, const int32_t* ib) {
+  while (f.pos >= f.end && f.seg <= 2 * f.D + 1) {
+    if (++f.seg > 2 * f.D + 1) break;
     const int it = seg_item(f.D, f.wi, f.seg);
     if (it >= 0) {
       const bool isL = f.seg <= f.D;
-      const int b0 = ib[4 * it + (isL ? 0 : 2)], b1 = ib[4 * it + (isL ? 1 : 3)];
-      if (b0 + f.off < b1) {
-        const int nb = min(SB, b1 - b0 - f.off);
-        const int st = f.issued % NST;
-        const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(ring + (size_t)st * SB * STR, (isL ? Lpack : Upack) + (size_t)(b0 + f.off) * STR, bytes,
-                 &full[st]);
-        f.off += nb;
-        f.issued++;
-        return;
-      }
+      f.pos = ib[4 * it + (isL ? 0 : 2)];
+      f.end = ib[4 * it + (isL ? 1 : 3)];
     }
-    f.seg++;
-    f.off = 0;
   }
+}
+
+// lane 0: issue the next stage of the warp's sequence (if any) into its ring slot.
+// The slot was last read by this warp's lanes, whose loads completed before the
+// __syncwarp that precedes every call.
+template <class TF, int STR>
+__device__ __forceinline__ void feed_issue(WarpFeed& f, const int32_t* ib, const TF* Lpack, const TF* Upack, TF* ring,
+                                           uint64_t* full, int NST, int SB) {
+  feed_seek(f, ib);
+  if (f.pos >= f.end) return;
+  const int nb = min(SB, f.end - f.pos);
+  const int st = f.issued % NST;
+  const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
+  mbar_arrive_expect_tx(&full[st], bytes);
+  bulk_g2s(ring + (size_t)st * SB * STR, (f.seg <= f.D ? Lpack : Upack) + (size_t)f.pos * STR, bytes, &full[st]);
+  f.pos += nb;
+  f.issued++;
 }
 
 // Multi-warp streamed RAS apply (Sec. 3, Eq. 16) on nested-dissection ordered
@@ -218,10 +223,10 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   }
   __syncthreads();
 
-  WarpFeed f{D, wi, 0, 0, 0, 0};
+  WarpFeed f{D, wi, -1, 0, 0, 0, 0};
   const bool active = wi < (1 << D);
   if (active && lane == 0 && !R.stall)
-    for (int k = 0; k < NST; ++k) feed_issue<TF, STR>(f, R, ib, Lpack, Upack, ring, full, NST, SB);
+    for (int k = 0; k < NST; ++k) feed_issue<TF, STR>(f, ib, Lpack, Upack, ring, full, NST, SB);
   f.issued = __shfl_sync(0xffffffffu, f.issued, 0);
 
   const int j = lane / 7, c = lane - 7 * (lane / 7);  // block slot 0..3 (4 = idle), component
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   auto release = [&]() {
     __syncwarp();
     f.used++;
-    if (lane == 0 && !R.stall) feed_issue<TF, STR>(f, R, ib, Lpack, Upack, ring, full, NST, SB);
+    if (lane == 0 && !R.stall) feed_issue<TF, STR>(f, ib, Lpack, Upack, ring, full, NST, SB);
     f.issued = __shfl_sync(0xffffffffu, f.issued, 0);
   };
 

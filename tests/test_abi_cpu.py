@@ -103,12 +103,47 @@ def test_create_rejects_bad_meshes_and_options_on_the_host():
 
 
 def test_autotune_default_grid():
-    """Subdomain counts are powers of two giving 40..1000 nodes per subdomain;
-    both ILU levels and both RCM orders are searched, overlap 1, one warp per row."""
-    from paper_1810_04289_gb300.autotune import default_grid
+    """Subdomain counts are powers of two giving 40..1000 nodes per subdomain; both
+    ILU levels, the three orderings that reorder (RCM, lumen-first RCM, nested
+    dissection), overlap 1 and 2 and both SpMV row mappings are searched."""
+    from paper_1810_04289_gb300.autotune import default_grid, KNOBS
     g = default_grid(46657)
     assert g["n_subdomains"] == (64, 128, 256, 512, 1024)
     assert all(40 <= 46657 / k <= 1000 for k in g["n_subdomains"])
-    assert g["ilu_level"] == (1, 2) and g["ordering"] == (1, 2)
-    assert g["overlap"] == (1,) and g["threads_per_row"] == (32,)
+    assert g["ilu_level"] == (1, 2) and g["ordering"] == (1, 2, 3)
+    assert g["overlap"] == (1, 2) and g["threads_per_row"] == (32, 16)
+    assert set(KNOBS) == set(g)
     assert default_grid(30)["n_subdomains"] == (1,)
+
+
+def test_autotune_coordinate_search_logic(monkeypatch):
+    """The coordinate search visits every value of every knob with the others at
+    their best so far, never times a candidate twice and returns the fastest
+    converged one (the timing is replaced by a fake cost on the CPU)."""
+    from paper_1810_04289_gb300 import autotune as A
+    from paper_1810_04289_gb300 import fsi
+
+    class FakeMesh:
+        n_nodes = 46657
+
+    calls = []
+
+    def fake(mesh, material, y0, opt, t0, torch):
+        key = (opt.n_subdomains, opt.ilu_level, opt.ordering, opt.overlap, opt.threads_per_row)
+        calls.append(key)
+        # converges except for ordering 3; cheapest at 512 subdomains, ILU(2), overlap 1, 16 per row
+        if opt.ordering == 3:
+            return dict(seconds=9.0, iterations=1000, converged=False)
+        t = abs(opt.n_subdomains - 512) / 512 + (0 if opt.ilu_level == 2 else 0.3) + 0.2 * (opt.overlap - 1)
+        t += 0.0 if opt.threads_per_row == 16 else 0.05
+        return dict(seconds=1.0 + t, iterations=100, converged=True)
+
+    monkeypatch.setattr(A, "_candidate", fake)
+    import sys
+    import types
+    monkeypatch.setitem(sys.modules, "torch", types.ModuleType("torch"))
+    best, table = A.autotune(FakeMesh(), {}, None, base=fsi.FsiOptions())
+    assert (best.n_subdomains, best.ilu_level, best.ordering, best.overlap, best.threads_per_row) == (512, 2, 1, 1, 16)
+    assert len(calls) == len(set(calls)) == len(table)
+    g = A.default_grid(46657)
+    assert len(calls) <= sum(len(v) for v in g.values()) * 2
