@@ -219,10 +219,11 @@ def ilu_levels(order, adj, fill):
 def block_ilu(A, keep):
     """Block ILU on the kept pattern (step 5). A: (m, m, 7, 7) blocks of J_i^delta,
     keep: (m, m) bool. Returns (A, Dinv): the strictly lower blocks of A hold L
-    (unit diagonal implied), the upper blocks U, Dinv the inverted pivots."""
+    (unit diagonal implied), the upper blocks U, Dinv the inverted pivots. The
+    arithmetic is in A's dtype."""
     A = A.copy()
     m = A.shape[0]
-    Dinv = np.zeros((m, 7, 7))
+    Dinv = np.zeros((m, 7, 7), dtype=A.dtype)
     for q in range(m):
         for k in range(q):
             if not keep[q, k]:
@@ -241,11 +242,13 @@ class RAS:
     J: scipy sparse (7N x 7N) Jacobian; X (N,3) reference coordinates; tets
     (T,4); node_problem (N,) or None; node_rank (N,) for ordering 2; adj: the
     node graph as a list of sorted neighbour arrays, in place of the one the
-    tetrahedra give (tests on plain graphs).
+    tetrahedra give (tests on plain graphs). dtype: the arithmetic of the
+    factorisation and the solves (FP64, or FP32 as in the mixed-precision form,
+    where the subdomain factors and solves are FP32 and the vectors FP64 outside).
     """
 
     def __init__(self, J, X, tets, node_problem, n_problems, n_sub, delta, fill, ordering, node_rank=None,
-                 adj=None):
+                 adj=None, dtype=np.float64):
         import scipy.sparse as sp
         N = np.asarray(X).shape[0]
         self.N = N
@@ -263,7 +266,7 @@ class RAS:
             m = len(order)
             dofs = (7 * order[:, None] + np.arange(7)[None, :]).reshape(-1)
             Jd = Jc[dofs][:, dofs].toarray().reshape(m, 7, m, 7).transpose(0, 2, 1, 3)
-            A = np.where(keep[:, :, None, None], Jd, 0.0)
+            A = np.where(keep[:, :, None, None], Jd, 0.0).astype(dtype)
             LU, Dinv = block_ilu(A, keep)
             self.subs.append(dict(order=order, owned=(owner[order] == s), keep=keep, LU=LU, Dinv=Dinv))
 
@@ -274,7 +277,7 @@ class RAS:
         for sd in self.subs:
             order, keep, LU, Dinv = sd["order"], sd["keep"], sd["LU"], sd["Dinv"]
             m = len(order)
-            w = r[order].copy()
+            w = r[order].astype(LU.dtype)
             for q in range(m):
                 for k in np.nonzero(keep[q, :q])[0]:
                     w[q] -= LU[q, k] @ w[k]
