@@ -842,7 +842,8 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
 
     // packed factor streams for the TMA-fed apply
     {
-      std::vector<int64_t> Lcnt(R.gnode.size()), Ucnt(R.gnode.size()), Loff(R.np + 1), Uoff(R.np + 1), Lsrc, Usrc;
+      std::vector<int64_t> Lcnt(R.gnode.size()), Ucnt(R.gnode.size()), Loff(R.np + 1), Uoff(R.np + 1), Lsrc, Usrc,
+          Upiv;
       std::vector<int32_t> Lcol, Ucol;
       int64_t maxblk = 1;
       for (int32_t sd = 0; sd < R.np; ++sd) {
@@ -860,9 +861,11 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
         for (int64_t q = b - 1; q >= a; --q) {
           Usrc.push_back(R.diag[q]);
           Ucol.push_back((int32_t)(q - a));
+          Upiv.push_back(-1);
           for (int64_t e = R.diag[q] + 1; e < R.row_ptr[q + 1]; ++e) {
             Usrc.push_back(e);
             Ucol.push_back((int32_t)(R.col[e] - a));
+            Upiv.push_back(R.diag[q]);
           }
           Ucnt[q] = R.row_ptr[q + 1] - R.diag[q];
           maxblk = std::max(maxblk, Ucnt[q]);
@@ -913,15 +916,16 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Lcol = cp->upload(Lcol);
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
+      rs.Upiv = cp->upload(Upiv);
       // stage geometry: NST stages of SB blocks. The subdomains should all be
       // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
       // shared memory per CTA leaves after the vector; the stage_blocks and
       // stages options override the choice
-      const int vsz = cp->mixed ? 4 : 8, stride = cp->mixed ? 52 : 50;
+      const int vsz = cp->mixed ? 4 : 8, stride = 56;  // packed block: 7 rows of 8 values
       int nst = o.stages > 0 ? o.stages : 3;
       const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
       const int64_t per_sm = std::min<int64_t>(8, (R.np + 151) / 152);
-      const int64_t fixed = 128 * ((W * 64 + 127) / 128) + 7 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
+      const int64_t fixed = 128 * ((W * 64 + 127) / 128) + 8 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
       // (the budget never exceeds the 200 KB the streamed apply may use)
       const int64_t budget = std::min<int64_t>((int64_t)(227 * 1024) / per_sm, (int64_t)(200 * 1024));
       int64_t SB = (budget - fixed) / (W * nst * stride * vsz);

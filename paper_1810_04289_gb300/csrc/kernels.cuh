@@ -116,6 +116,7 @@ struct RasStreamDev {
   const int32_t* Lcol;    // [nL] subdomain-relative column row
   const int64_t* Usrc;
   const int32_t* Ucol;
+  const int64_t* Upiv;    // [nU] factor block of the row's inverted pivot, -1 for the pivot itself
   int32_t stage_blocks;   // blocks per ring stage (one bulk copy; rows may straddle stages)
   int64_t max_rows;       // rows of the largest subdomain
   int32_t nst;            // ring stages in flight per warp (2..8)

@@ -11,9 +11,12 @@
 //
 // Packed layout (built by k_pack_factors after each factorisation):
 //   L stream: for every row in increasing order, its L blocks;
-//   U stream: for every row in decreasing order, its inverted pivot, then its U blocks.
-// Each packed block holds 49 values, then the subdomain-relative column row in
-// the first 4 bytes of slot 49, padded to a 16-byte multiple (52 floats, 50 doubles).
+//   U stream: for every row in decreasing order, its inverted pivot D_q^{-1}, then
+//             its U blocks premultiplied and negated, -D_q^{-1} U_qj.
+// Each packed block holds its 7 rows as 8-wide, 16-byte aligned rows (56 values):
+// the row's 7 entries, then one slot; row 0's slot holds the subdomain-relative
+// column row (as int bits). The subdomain vector in shared memory is 8 wide too,
+// so each 7-term product is four 16-byte loads (FP32) instead of fourteen.
 // Stages are fixed slices of stage_blocks blocks of a subdomain's L stream, then
 // of its U stream; a row may straddle stages (its partial sums carry over), so
 // the stage size is independent of the row length and can be chosen for
@@ -74,12 +77,35 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 template <class TF> struct Pack;
-template <> struct Pack<float> { static constexpr int stride = 52; };
-template <> struct Pack<double> { static constexpr int stride = 50; };
+// packed block: 7 rows of 8 values (the 7 entries of the row, then one slot),
+// 16-byte aligned rows; the slot of row 0 holds the column (as int bits), the
+// other slots are zero
+template <class TF> struct Pack { static constexpr int stride = 56; };
 
 template <class TF>
 __device__ __forceinline__ int blk_col(const TF* blk) {
-  return *reinterpret_cast<const int*>(blk + 49);
+  return *reinterpret_cast<const int*>(blk + 7);
+}
+
+// the 7-term product of row c of a packed block with the node vector x (8 wide):
+// 16-byte loads of the row and of x
+__device__ __forceinline__ float row7(const float* a, const float* x) {
+  const float4 a0 = *reinterpret_cast<const float4*>(a), a1 = *reinterpret_cast<const float4*>(a + 4);
+  const float4 x0 = *reinterpret_cast<const float4*>(x), x1 = *reinterpret_cast<const float4*>(x + 4);
+  const float p01 = a0.x * x0.x + a0.y * x0.y;
+  const float p23 = a0.z * x0.z + a0.w * x0.w;
+  const float p45 = a1.x * x1.x + a1.y * x1.y;
+  return (p01 + p23) + (p45 + a1.z * x1.z);
+}
+__device__ __forceinline__ double row7(const double* a, const double* x) {
+  const double2 a0 = *reinterpret_cast<const double2*>(a), a1 = *reinterpret_cast<const double2*>(a + 2);
+  const double2 a2 = *reinterpret_cast<const double2*>(a + 4), a3 = *reinterpret_cast<const double2*>(a + 6);
+  const double2 x0 = *reinterpret_cast<const double2*>(x), x1 = *reinterpret_cast<const double2*>(x + 2);
+  const double2 x2 = *reinterpret_cast<const double2*>(x + 4), x3 = *reinterpret_cast<const double2*>(x + 6);
+  const double p01 = a0.x * x0.x + a0.y * x0.y;
+  const double p23 = a1.x * x1.x + a1.y * x1.y;
+  const double p45 = a2.x * x2.x + a2.y * x2.y;
+  return (p01 + p23) + (p45 + a3.x * x3.x);
 }
 
 constexpr int NSTMAX = 8;  // most ring stages (runtime count R.nst)
@@ -87,7 +113,8 @@ constexpr int NSTMAX = 8;  // most ring stages (runtime count R.nst)
 // sum over blocks b in [b0, nb) of (block b, row c) . w[col(b)], reduced over
 // the warp: lane = 7 j + c handles blocks b0 + j, b0 + j + 4, ...; every block
 // gathers its column index first so that all loads of a chunk are independent,
-// then forms the 7-term products as a short tree. The total lands in lanes 0..6.
+// then forms the 7-term products (16-byte loads of the block row and of the
+// 8-wide node vector). The total lands in lanes 0..6.
 template <class TF, int STR>
 __device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w, int j, int c) {
   TF acc = TF(0);
@@ -103,14 +130,7 @@ __device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (cols[i] >= 0) {
-          const TF* a = blk[i] + 7 * c;
-          const TF* x = w + 7 * cols[i];
-          const TF p01 = a[0] * x[0] + a[1] * x[1];
-          const TF p23 = a[2] * x[2] + a[3] * x[3];
-          const TF p45 = a[4] * x[4] + a[5] * x[5];
-          acc += (p01 + p23) + (p45 + a[6] * x[6]);
-        }
+        if (cols[i] >= 0) acc += row7(blk[i] + 8 * c, w + 8 * cols[i]);
       }
     }
   }
@@ -195,7 +215,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   TF* rings = reinterpret_cast<TF*>(smem + 128 * ((nwarps * NSTMAX * 8 + 127) / 128));
   TF* ring = rings + (size_t)wi * NST * SB * STR;
   TF* w = rings + (size_t)nwarps * NST * SB * STR;
-  unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 7 * (size_t)R.max_rows);
+  unsigned short* Lcnt = reinterpret_cast<unsigned short*>(w + 8 * (size_t)R.max_rows);
   unsigned short* Ucnt = Lcnt + R.max_rows;
   uint64_t* full = bars + wi * NSTMAX;
   const int s = blockIdx.x;
@@ -217,7 +237,8 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
 #pragma unroll
     for (int c = 0; c < 7; ++c) v[c] = src[c];
 #pragma unroll
-    for (int c = 0; c < 7; ++c) w[7 * q + c] = (TF)v[c];
+    for (int c = 0; c < 7; ++c) w[8 * q + c] = (TF)v[c];
+    w[8 * q + 7] = TF(0);
     Lcnt[q] = (unsigned short)R.L_cnt[r0 + q];
     Ucnt[q] = (unsigned short)R.U_cnt[r0 + q];
   }
@@ -265,7 +286,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
           pos = k;
           rem -= k;
           if (rem == 0) {
-            if (lane < 7) w[7 * q + lane] -= acc;
+            if (lane < 7) w[8 * q + lane] -= acc;
             __syncwarp();
             ++q;
           }
@@ -275,7 +296,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
             const int nb = Lcnt[q];
             if (pos + nb > cap) break;
             const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
-            if (lane < 7 && nb > 0) w[7 * q + lane] -= a;
+            if (lane < 7 && nb > 0) w[8 * q + lane] -= a;
             __syncwarp();
             pos += nb;
           }
@@ -290,7 +311,10 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
     }
     __syncthreads();
   }
-  // backward: phases D..0, w_q = D_q^{-1} (w_q - sum_j U_qj w_j), pivot first in each row
+  // backward: phases D..0, w_q = D_q^{-1} w_q - sum_j (D_q^{-1} U_qj) w_j: the
+  // U stream holds, per row, the inverted pivot (column q: it multiplies the
+  // forward result still in w_q) and then the blocks -D_q^{-1} U_qj, so a row is
+  // one dot product over its blocks, as in the forward solve
   for (int p = D; p >= 0; --p) {
     const int it = seg_item(D, wi, 2 * D + 1 - p);
     if (it >= 0 && ok) {
@@ -299,24 +323,6 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
       const int nUb = ib[4 * it + 3] - ib[4 * it + 2];
       int rem = 0, done = 0;
       TF acc = TF(0);
-      TF dreg[7];
-      auto finish = [&](int row, TF sum) {
-        const TF t = (lane < 7) ? w[7 * row + lane] - sum : TF(0);
-        TF tv[7];
-#pragma unroll
-        for (int mm = 0; mm < 7; ++mm) tv[mm] = __shfl_sync(0xffffffffu, t, mm);
-        if (lane < 7) {
-          TF zz = TF(0);
-#pragma unroll
-          for (int mm = 0; mm < 7; ++mm) zz += dreg[mm] * tv[mm];
-          w[7 * row + lane] = zz;
-        }
-        __syncwarp();
-      };
-      auto load_pivot = [&](const TF* blk) {
-#pragma unroll
-        for (int mm = 0; mm < 7; ++mm) dreg[mm] = lane < 7 ? blk[7 * lane + mm] : TF(0);
-      };
       while (done < nUb) {
         const TF* stg = next_stage();
         if (!stg) { ok = false; break; }
@@ -328,7 +334,8 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
           pos = k;
           rem -= k;
           if (rem == 0) {
-            finish(q, acc);
+            if (lane < 7) w[8 * q + lane] = acc;
+            __syncwarp();
             --q;
           }
         }
@@ -336,15 +343,13 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
           for (; q >= qb; --q) {
             const int nb = Ucnt[q];
             if (pos + nb > cap) break;
-            const TF* rs = stg + (size_t)pos * STR;
-            load_pivot(rs);
-            finish(q, row_dot<TF, STR>(rs, 1, nb, w, j, c));
+            const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
+            if (lane < 7) w[8 * q + lane] = a;
+            __syncwarp();
             pos += nb;
           }
           if (q >= qb && pos < cap) {
-            const TF* rs = stg + (size_t)pos * STR;
-            load_pivot(rs);
-            acc = row_dot<TF, STR>(rs, 1, cap - pos, w, j, c);
+            acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
             rem = Ucnt[q] - (cap - pos);
           }
         }
@@ -368,33 +373,49 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
     if (R.owned[r0 + q]) {
       const int64_t g7 = 7 * (int64_t)R.gnode[r0 + q];
 #pragma unroll
-      for (int cc = 0; cc < 7; ++cc) z[g7 + cc] = (double)w[7 * q + cc];
+      for (int cc = 0; cc < 7; ++cc) z[g7 + cc] = (double)w[8 * q + cc];
       if (z32) {
 #pragma unroll
-        for (int cc = 0; cc < 7; ++cc) z32[g7 + cc] = (float)w[7 * q + cc];
+        for (int cc = 0; cc < 7; ++cc) z32[g7 + cc] = (float)w[8 * q + cc];
       }
     }
   }
 }
 
-// copy the factor blocks into the packed streams
+// copy the factor blocks into the packed streams (7 rows of 8: the row's 7
+// entries, then the column index in row 0's last slot, zeros in the others); a
+// U block with a pivot (Upiv >= 0) is stored as -D_q^{-1} U_qj, the row's
+// inverted pivot itself as it is
 template <class TF>
 __global__ void k_pack_factors(int64_t nL, const int64_t* __restrict__ Lsrc, const int32_t* __restrict__ Lcol,
                                int64_t nU, const int64_t* __restrict__ Usrc, const int32_t* __restrict__ Ucol,
-                               const TF* __restrict__ fac, TF* __restrict__ Lpack, TF* __restrict__ Upack) {
+                               const int64_t* __restrict__ Upiv, const TF* __restrict__ fac, TF* __restrict__ Lpack,
+                               TF* __restrict__ Upack) {
   constexpr int STR = Pack<TF>::stride;
   const int64_t total = (nL + nU) * STR;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = idx / STR;
     const int e = (int)(idx - STR * b);
+    const int r = e >> 3, k = e & 7;
     const bool isL = b < nL;
     const int64_t bb = isL ? b : b - nL;
     const int64_t src = isL ? Lsrc[bb] : Usrc[bb];
     TF* dst = (isL ? Lpack : Upack) + bb * STR;
-    if (e < 49) {
-      dst[e] = fac[49 * src + e];
-    } else if (e == 49) {
+    if (k < 7) {
+      const int64_t piv = isL ? -1 : Upiv[bb];
+      if (piv < 0) {
+        dst[e] = fac[49 * src + 7 * r + k];
+      } else {
+        // -(D_q^{-1} U_qj)[r][k]
+        const TF* Dq = fac + 49 * piv + 7 * r;
+        const TF* U = fac + 49 * src + k;
+        TF v = TF(0);
+#pragma unroll
+        for (int mm = 0; mm < 7; ++mm) v += Dq[mm] * U[7 * mm];
+        dst[e] = -v;
+      }
+    } else if (r == 0) {
       TF v = TF(0);
       *reinterpret_cast<int*>(&v) = isL ? Lcol[bb] : Ucol[bb];
       dst[e] = v;
@@ -410,7 +431,7 @@ template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r) {
   const size_t W = (size_t)1 << r.max_depth;
   return 128 * ((W * NSTMAX * 8 + 127) / 128) + W * r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) +
-         (size_t)7 * r.max_rows * sizeof(TF) + (size_t)4 * r.max_rows + 16;
+         (size_t)8 * r.max_rows * sizeof(TF) + (size_t)4 * r.max_rows + 16;
 }
 
 template <class TF>
@@ -418,8 +439,8 @@ void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s) {
   const int64_t total = (r.nL + r.nU) * Pack<TF>::stride;
   int64_t g = (total + 255) / 256;
   if (g > 152 * 64) g = 152 * 64;
-  k_pack_factors<TF><<<(int)g, 256, 0, s>>>(r.nL, r.Lsrc, r.Lcol, r.nU, r.Usrc, r.Ucol, fac, (TF*)r.Lpack,
-                                            (TF*)r.Upack);
+  k_pack_factors<TF><<<(int)g, 256, 0, s>>>(r.nL, r.Lsrc, r.Lcol, r.nU, r.Usrc, r.Ucol, r.Upiv, fac,
+                                            (TF*)r.Lpack, (TF*)r.Upack);
 }
 
 template <class TF>
