@@ -49,6 +49,14 @@ METRIC = "FSI time steps/s on 1 GB300, mixed-precision vs FP64 at Newton rtol 1e
 # the Jacobian lag by timing whole steps) on a GB300, committed so that the
 # benchmark does not repeat the search; --autotune searches again.
 TUNED = {
+    # 15.8 M-unknown tree: one-level RAS iterations barely grow from 4,096 to
+    # 16,384 subdomains (the ILU quality sets them), so the shortest sequential
+    # chains win; ILU(1) beats ILU(2) per step (fewer factor bytes per apply,
+    # about 5% more iterations); one Jacobian and its factors per step (lag 3)
+    ("tree-3gen", "mixed"): dict(n_subdomains=16384, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                 jac_lag=3),
+    ("tree-3gen", "fp64"): dict(n_subdomains=16384, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                jac_lag=3),
     ("tube-96x32x15", "mixed"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                      jac_lag=3),
     ("tube-96x32x15", "fp64"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,

@@ -147,7 +147,12 @@ typedef struct {
                              up to the order of the row sums. */
   int32_t stage_blocks;   /* streamed apply: factor blocks per ring stage, 0 = automatic
                              (sized so that every subdomain's CTA is resident) */
-  int32_t stages;         /* streamed apply: ring stages in flight, 2..8, 0 = automatic (3) */
+  int32_t stages;         /* streamed apply: ring stages in flight per warp, 2..8,
+                             0 = automatic (3) */
+  int32_t orth;           /* Arnoldi orthogonalisation: 0 classical Gram-Schmidt twice;
+                             1 classical Gram-Schmidt with a second pass only where the
+                             first removed more than 1 - 1/sqrt(2) of the vector's norm
+                             (selective reorthogonalisation) */
 } fsi_options;
 
 typedef struct {

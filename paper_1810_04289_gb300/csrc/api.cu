@@ -96,6 +96,7 @@ struct fsi_ctx {
   int* active = nullptr;         // [P] problem still iterating in the cycle
   int* kcols = nullptr;          // [P] Krylov columns built in the cycle
   int* anyact = nullptr;         // [1] some problem active (guard of the captured kernels)
+  int* reorth = nullptr;         // [1] some problem needs a second Gram-Schmidt pass (orth = 1)
   int* pmask = nullptr;          // [P] problem already converged (Newton)
   double* palpha = nullptr;      // [P] line-search step per problem
   float* zf = nullptr;           // FP32 copy of the SpMV input (mixed precision)
@@ -334,6 +335,23 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
   const int64_t n = c->n;
   const int32_t m = c->m, ldh = m + 1, P = c->nprob;
   double* w = c->V + (int64_t)(j + 1) * n;
+  if (c->opt.orth == 1) {
+    // classical Gram-Schmidt with a second pass only where the first removed more
+    // than 1 - 1/sqrt(2) of ||w|| (the pass-2 kernels are guarded by that test)
+    double* hj = c->H + (int64_t)j * ldh + j + 1;
+    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st, 1);
+    launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
+    launch_seg_norm(c->seg, w, c->partial, hj, ldh * m, guard, st);
+    launch_seg_reorth_decide(P, c->hA + j + 1, hj, ldh * m, c->hB, ldh, j, c->active, c->reorth, st);
+    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, c->reorth, st);
+    launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, c->reorth, st);
+    launch_seg_norm(c->seg, w, c->partial, hj, ldh * m, c->reorth, st);
+    launch_seg_scale_inv(c->seg, n, w, hj, ldh * m, w, guard, st);
+    launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
+                      c->kcols, c->anyact, st);
+    c->launches += 9;
+    return;
+  }
   launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
   launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
@@ -487,6 +505,7 @@ void fill_defaults(fsi_options* o) {
   o->apply_mode = 0;
   o->stage_blocks = 0;
   o->stages = 0;
+  o->orth = 0;
 }
 
 }  // namespace
@@ -532,7 +551,9 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       o.apply_mode = q.apply_mode;
       o.stage_blocks = q.stage_blocks;
       o.stages = q.stages;
+      o.orth = q.orth;
     }
+    if (o.orth != 0 && o.orth != 1) throw StatusError{FSI_ERR_ARG, "orth must be 0 or 1"};
     if (o.apply_mode < 0 || o.apply_mode > 2) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0, 1 or 2"};
     if (o.stage_blocks < 0) throw StatusError{FSI_ERR_ARG, "stage_blocks must be >= 0"};
     if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) throw StatusError{FSI_ERR_ARG, "stages must be 0 or 2..8"};
@@ -704,7 +725,10 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
         cp->Xl = cp->upload(xl);
       }
     }
-    cp->Ke = cp->dalloc<char>((int64_t)(784 * vs) * T0);
+    // the element Jacobian buffer Ke and the subdomain factors share one
+    // allocation (sized below, once the factor size is known): Ke is live only
+    // inside a Jacobian assembly, the factors only from the preconditioner
+    // setup that follows it (every assembly marks the preconditioner stale)
     cp->vals = cp->dalloc<char>((int64_t)(49 * vs) * cp->nnzb);
     CK(cudaMemsetAsync(cp->vals, 0, 49 * vs * cp->nnzb, cp->s));
     cp->mesh = MeshDev{N, T0, Tf, cp->X, cp->tets, cp->nflag, cp->nprobid, cp->inlet};
@@ -770,6 +794,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->active = cp->dalloc<int>(n_problems);
     cp->kcols = cp->dalloc<int>(n_problems);
     cp->anyact = cp->dalloc<int>(1);
+    cp->reorth = cp->dalloc<int>(1);
     cp->pmask = cp->dalloc<int>(n_problems);
     cp->palpha = cp->dalloc<double>(n_problems);
     cp->r = cp->dalloc<double>(n);
@@ -835,7 +860,8 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
 
     }
     cp->ras = rd;
-    cp->fac = cp->dalloc<char>((int64_t)(49 * vs) * rd.nblocks);
+    cp->fac = cp->dalloc<char>(std::max<int64_t>((int64_t)(49 * vs) * rd.nblocks, (int64_t)(784 * vs) * T0));
+    cp->Ke = cp->fac;
     cp->work = cp->dalloc<char>((int64_t)(7 * vs) * (int64_t)R.gnode.size());
     cp->errflag = cp->dalloc<int32_t>(2);
     CK(cudaMemsetAsync(cp->errflag, 0, 2 * sizeof(int32_t), cp->s));
@@ -917,6 +943,10 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
       rs.Upiv = cp->upload(Upiv);
+      // stage geometry: NST stages of SB blocks. The subdomains should all be
+      // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
+      // shared memory per CTA leaves after the vector; the stage_blocks and
+      // stages options override the choice
       // stage geometry: NST stages of SB blocks. The subdomains should all be
       // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
       // shared memory per CTA leaves after the vector; the stage_blocks and

@@ -35,10 +35,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 // for vectors 8y .. 8y+7; the last block of problem p for group y sums the
 // problem's partials (one warp per vector, lanes over the chunks in fixed order)
 // and resets the counter.
+// With nself = 1 there is one more output, index nv_v = nv - 1: w . w itself.
 __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const double* __restrict__ V, int64_t ldv,
                                                  const double* __restrict__ w, double* __restrict__ partial,
                                                  double* __restrict__ out, int32_t ldo, int take_sqrt,
-                                                 const int* guard) {
+                                                 int nself, const int* guard) {
   if (off(guard)) return;
   __shared__ double red[MD][RB / 32];
   __shared__ int s_last;
@@ -48,11 +49,12 @@ __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const do
   double acc[MD];
 #pragma unroll
   for (int k = 0; k < MD; ++k) acc[k] = 0.0;
+  const int nvv = nv - nself;  // vectors of V; the rest is w itself
   for (int64_t i = i0 + threadIdx.x; i < i1; i += RB) {
     const double wi = w[i];
 #pragma unroll
     for (int k = 0; k < MD; ++k)
-      if (k0 + k < nv) acc[k] += (V ? V[(int64_t)(k0 + k) * ldv + i] : wi) * wi;
+      if (k0 + k < nv) acc[k] += ((V && k0 + k < nvv) ? V[(int64_t)(k0 + k) * ldv + i] : wi) * wi;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -124,6 +126,28 @@ __global__ void k_seg_cycle_init(int32_t P, double* __restrict__ g, int32_t ldg,
   }
   __syncthreads();
   if (threadIdx.x == 0) *any = s_any;
+}
+
+// Selective reorthogonalisation (the criterion of Daniel, Gragg, Kaufman and
+// Stewart, 1976): after one classical Gram-Schmidt pass, a second pass is needed
+// where the pass removed more than 1 - 1/sqrt(2) of the vector's norm, i.e.
+// where ||w_after||^2 < ||w_before||^2 / 2. For every active problem p: s0 =
+// ||w_before||^2 (ws[p * lda]), t = ||w_after|| (nrm[p * ldn]); the second-pass
+// coefficients hb[p][0..j] are zeroed (a second pass, if it runs, overwrites
+// them); *flag = some active problem needs the second pass.
+__global__ void k_seg_reorth_decide(int32_t P, const double* __restrict__ ws, const double* __restrict__ nrm,
+                                    int32_t ldn, double* __restrict__ hb, int32_t lda, int32_t j,
+                                    const int* __restrict__ active, int* __restrict__ flag) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    for (int i = 0; i <= j; ++i) hb[(int64_t)p * lda + i] = 0.0;
+    const double s0 = ws[(int64_t)p * lda], t = nrm[(int64_t)p * ldn];
+    if (active[p] && t * t < 0.5 * s0) atomicOr(&s_any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = s_any;
 }
 
 // Givens update of column j of every active problem's Hessenberg (formed here
@@ -244,15 +268,21 @@ inline int grid_for(int64_t work, int block) {
 }  // namespace
 
 void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                     double* out, int32_t ldo, const int* guard, cudaStream_t s) {
-  dim3 grid((unsigned)sg.n_chunks, (nv + MD - 1) / MD);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, nv, V, ldv, w, partial, out, ldo, 0, guard);
+                     double* out, int32_t ldo, const int* guard, cudaStream_t s, int with_self) {
+  const int n = nv + (with_self ? 1 : 0);
+  dim3 grid((unsigned)sg.n_chunks, (n + MD - 1) / MD);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, n, V, ldv, w, partial, out, ldo, 0, with_self ? 1 : 0, guard);
 }
 
 void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
                      const int* guard, cudaStream_t s) {
   dim3 grid((unsigned)sg.n_chunks, 1);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, out, ldo, 1, guard);
+  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, out, ldo, 1, 0, guard);
+}
+
+void launch_seg_reorth_decide(int32_t P, const double* ws, const double* nrm, int32_t ldn, double* hb, int32_t lda,
+                              int32_t j, const int* active, int* flag, cudaStream_t s) {
+  k_seg_reorth_decide<<<1, 256, 0, s>>>(P, ws, nrm, ldn, hb, lda, j, active, flag);
 }
 
 void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,

@@ -236,3 +236,20 @@ def test_newton_steps_with_jacobian_lag_match_oracle(tube0, oracle_tube0_steps):
         assert st.converged == 1
         assert st.jacobian_evaluations <= -(-st.newton_iterations // 3)
         assert all(v < 1e-8 for v in rel.values()), (k, rel)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+def test_newton_steps_with_selective_reorthogonalisation_match_oracle(tube0, oracle_tube0_steps, precision, tol):
+    """orth = 1 (Gram-Schmidt with a second pass only where the first lost more
+    than 1 - 1/sqrt(2) of the norm) changes the Krylov basis only at rounding
+    level: the Newton steps still match the oracle's."""
+    y0, ref = oracle_tube0_steps
+    S = make_solver(tube0, precision=precision, newton_rtol=1e-10, gmres_rtol=1e-6 if precision == 0 else 1e-4,
+                    n_subdomains=4, orth=1)
+    S.set_state(y0, t=0.0)
+    for k in range(5):
+        st = S.step()
+        y, _ = S.state()
+        rel = rel_by_group(y, ref[k])
+        assert st.converged == 1
+        assert all(v < tol for v in rel.values()), (k, rel)
