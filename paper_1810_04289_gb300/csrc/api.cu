@@ -64,6 +64,7 @@ struct fsi_ctx {
   int32_t *nsrc = nullptr, *bsrc = nullptr;
   double* Fe = nullptr;
   void* Ke = nullptr;
+  int64_t ke_tets = 0;        // tets per chunk of the element Jacobian buffer
   void* Xl = nullptr;         // per-tet local reference coordinates, Jacobian type
   float* y32 = nullptr;       // mixed: FP32 copies of y, y_n, y_{n-1} for the Jacobian
   int64_t* row_ptr = nullptr;
@@ -239,13 +240,23 @@ void jacobian(fsi_ctx* c, const double* y) {
   if (c->mixed) {
     c->launches += 1;
     launch_states_to_float(c->n, y, c->yn, c->ynm1, c->y32, c->s);
-    launch_elem_jacobian<float>(c->mesh, c->mc, (const float*)c->Xl, c->y32, c->y32 + c->n, c->y32 + 2 * c->n,
-                                (float*)c->Ke, c->s);
-    launch_gather_jacobian<float>(c->nnzb, c->bptr, c->bsrc, (const float*)c->Ke, (float*)c->vals, c->s);
+    for (int64_t t0 = 0; t0 < c->T; t0 += c->ke_tets) {
+      const int64_t t1 = std::min(c->T, t0 + c->ke_tets);
+      launch_elem_jacobian<float>(c->mesh, c->mc, (const float*)c->Xl, c->y32, c->y32 + c->n, c->y32 + 2 * c->n,
+                                  (float*)c->Ke, t0, t1, c->s);
+      launch_gather_jacobian<float>(c->nnzb, c->bptr, c->bsrc, (const float*)c->Ke, (float*)c->vals, t0, t1, c->s);
+      c->launches += t0 > 0 ? 2 : 0;
+    }
     launch_constraint_jacobian<float>(c->mesh, c->mc, c->diag, (float*)c->vals, c->s);
   } else {
-    launch_elem_jacobian<double>(c->mesh, c->mc, (const double*)c->Xl, y, c->yn, c->ynm1, (double*)c->Ke, c->s);
-    launch_gather_jacobian<double>(c->nnzb, c->bptr, c->bsrc, (const double*)c->Ke, (double*)c->vals, c->s);
+    for (int64_t t0 = 0; t0 < c->T; t0 += c->ke_tets) {
+      const int64_t t1 = std::min(c->T, t0 + c->ke_tets);
+      launch_elem_jacobian<double>(c->mesh, c->mc, (const double*)c->Xl, y, c->yn, c->ynm1, (double*)c->Ke, t0, t1,
+                                   c->s);
+      launch_gather_jacobian<double>(c->nnzb, c->bptr, c->bsrc, (const double*)c->Ke, (double*)c->vals, t0, t1,
+                                     c->s);
+      c->launches += t0 > 0 ? 2 : 0;
+    }
     launch_constraint_jacobian<double>(c->mesh, c->mc, c->diag, (double*)c->vals, c->s);
   }
   check_launch();
@@ -506,6 +517,7 @@ void fill_defaults(fsi_options* o) {
   o->stage_blocks = 0;
   o->stages = 0;
   o->orth = 0;
+  o->jac_chunk = 0;
 }
 
 }  // namespace
@@ -552,9 +564,11 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       o.stage_blocks = q.stage_blocks;
       o.stages = q.stages;
       o.orth = q.orth;
+      o.jac_chunk = q.jac_chunk;
     }
+    if (o.jac_chunk < 0) throw StatusError{FSI_ERR_ARG, "jac_chunk must be >= 0"};
     if (o.orth != 0 && o.orth != 1) throw StatusError{FSI_ERR_ARG, "orth must be 0 or 1"};
-    if (o.apply_mode < 0 || o.apply_mode > 2) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0, 1 or 2"};
+    if (o.apply_mode < 0 || o.apply_mode > 3) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0..3"};
     if (o.stage_blocks < 0) throw StatusError{FSI_ERR_ARG, "stage_blocks must be >= 0"};
     if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) throw StatusError{FSI_ERR_ARG, "stages must be 0 or 2..8"};
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
@@ -860,8 +874,17 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
 
     }
     cp->ras = rd;
-    cp->fac = cp->dalloc<char>(std::max<int64_t>((int64_t)(49 * vs) * rd.nblocks, (int64_t)(784 * vs) * T0));
-    cp->Ke = cp->fac;
+    // the Jacobian is assembled in chunks of tets so that Ke needs no more than
+    // the factors' size (or 1 GB): the shared buffer is as large as the factors
+    {
+      const int64_t fac_bytes = (int64_t)(49 * vs) * rd.nblocks;
+      const int64_t per_tet = (int64_t)(784 * vs);
+      const int64_t room = std::max<int64_t>(fac_bytes, (int64_t)1 << 30);
+      cp->ke_tets = std::max<int64_t>(1, std::min<int64_t>(T0, room / per_tet));
+      if (o.jac_chunk > 0) cp->ke_tets = std::min<int64_t>(T0, o.jac_chunk);
+      cp->fac = cp->dalloc<char>(std::max<int64_t>(fac_bytes, per_tet * cp->ke_tets));
+      cp->Ke = cp->fac;
+    }
     cp->work = cp->dalloc<char>((int64_t)(7 * vs) * (int64_t)R.gnode.size());
     cp->errflag = cp->dalloc<int32_t>(2);
     CK(cudaMemsetAsync(cp->errflag, 0, 2 * sizeof(int32_t), cp->s));
@@ -962,13 +985,33 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       SB = std::max<int64_t>(W > 1 ? 8 : 16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
       if (o.stage_blocks > 0) SB = o.stage_blocks;
       (void)maxblk;
+      rs.pair = (R.max_depth == 0 && o.apply_mode != 3) ? 1 : 0;
+      if (rs.pair) {
+        // paired-warp kernel: NST stages of SB blocks, both powers of two, a row
+        // spanning at most NST stages ((NST - 1) SB + 1 >= the longest row part);
+        // SB as large as the shared memory left per CTA allows (every CTA resident)
+        const int64_t pfixed = 256 + 8 * R.max_rows * vsz + 8 * (R.max_rows + 1) + 16 + 1024;
+        const int64_t pbudget = std::min<int64_t>((int64_t)(227 * 1024) / per_sm, (int64_t)(200 * 1024));
+        nst = o.stages > 0 ? o.stages : 4;
+        if (nst & (nst - 1)) throw StatusError{FSI_ERR_ARG, "stages must be a power of two for this apply"};
+        SB = 8;
+        while (SB * 2 * nst * stride * vsz + pfixed <= pbudget && SB < (cp->mixed ? 64 : 32)) SB *= 2;
+        if (o.stage_blocks > 0) {
+          SB = o.stage_blocks;
+          if (SB & (SB - 1)) throw StatusError{FSI_ERR_ARG, "stage_blocks must be a power of two for this apply"};
+        }
+        while ((nst - 1) * SB + 1 < maxblk) {
+          if (o.stages == 0 && nst < 8) nst *= 2;
+          else SB *= 2;
+        }
+      }
       rs.nst = nst;
       rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
       const bool fits = sm <= 200 * 1024;
-      if (o.apply_mode == 1 && !fits)
+      if ((o.apply_mode == 1 || o.apply_mode == 3) && !fits)
         throw StatusError{FSI_ERR_ARG, "apply_mode 1: the streamed apply's shared memory does not fit"};
       cp->use_stream = o.apply_mode == 2 ? false : fits;
       if (cp->use_stream) {
@@ -1261,7 +1304,7 @@ fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
   info->device_bytes = c->dev_bytes;
   info->n_wss_faces = c->nwss;
   info->nd_depth = c->plan.max_depth;
-  info->apply_kernel = c->use_stream ? 1 : 2;
+  info->apply_kernel = c->use_stream ? (c->rs.pair ? 1 : 3) : 2;
   return FSI_OK;
 }
 

@@ -158,11 +158,11 @@ constexpr int JAC_TETS_PER_BLOCK = 8;
 template <class T>
 __global__ void __launch_bounds__(28 * JAC_TETS_PER_BLOCK)
 k_elem_jacobian(MeshDev m, MatConst mc, const T* __restrict__ Xl, const T* __restrict__ y,
-                const T* __restrict__ y1, const T* __restrict__ y2, T* __restrict__ Ke) {
+                const T* __restrict__ y1, const T* __restrict__ y2, T* __restrict__ Ke, int64_t t0, int64_t t1) {
   const int tl = threadIdx.x / 28;
   const int colid = threadIdx.x - 28 * tl;
   const int b = colid / 7, k = colid - 7 * (colid / 7);
-  for (int64_t t = blockIdx.x * (int64_t)JAC_TETS_PER_BLOCK + tl; t < m.T;
+  for (int64_t t = t0 + blockIdx.x * (int64_t)JAC_TETS_PER_BLOCK + tl; t < t1;
        t += (int64_t)gridDim.x * JAC_TETS_PER_BLOCK) {
     int n[4];
     uint32_t f[4];
@@ -227,8 +227,8 @@ k_elem_jacobian(MeshDev m, MatConst mc, const T* __restrict__ Xl, const T* __res
         }
       }
     }
-    // Ke[t][a][b][r][k]
-    T* o = Ke + 784 * t + 49 * b + k;
+    // Ke[t - t0][a][b][r][k]
+    T* o = Ke + 784 * (t - t0) + 49 * b + k;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -245,15 +245,26 @@ __global__ void k_states_to_float(int64_t n, const double* __restrict__ a, const
   }
 }
 
+// Sum into each block the element blocks of the tets [t0, t1) (the buffer holds
+// those tets only). Each block's contributions are listed in increasing tet
+// order, so a chunk of tets is a contiguous part of every list; the first chunk
+// starts the sum at zero, the next ones continue it from vals, so the additions
+// happen in the same order as in a single pass (bitwise the same result).
 template <class T>
 __global__ void k_gather_jacobian(int64_t nnzb, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bsrc,
-                                  const T* __restrict__ Ke, T* __restrict__ vals) {
+                                  const T* __restrict__ Ke, T* __restrict__ vals, int64_t t0, int64_t t1) {
+  const int64_t lo = 16 * t0, hi = 16 * t1;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 49 * nnzb;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t kb = idx / 49;
     const int e = (int)(idx - 49 * kb);
-    T s = T(0);
-    for (int64_t c = bptr[kb]; c < bptr[kb + 1]; ++c) s += Ke[49 * (int64_t)bsrc[c] + e];
+    T s = t0 == 0 ? T(0) : vals[idx];
+    for (int64_t c = bptr[kb]; c < bptr[kb + 1]; ++c) {
+      const int64_t src = bsrc[c];
+      if (src < lo) continue;
+      if (src >= hi) break;
+      s += Ke[49 * (src - lo) + e];
+    }
     vals[idx] = s;
   }
 }
@@ -299,11 +310,11 @@ void launch_constraint_residual(const MeshDev& m, const MatConst& mc, double t, 
 
 template <class T>
 void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const T* Xl, const T* y, const T* y1, const T* y2,
-                          T* Ke, cudaStream_t s) {
-  if (m.T == 0) return;
-  int64_t blocks = (m.T + JAC_TETS_PER_BLOCK - 1) / JAC_TETS_PER_BLOCK;
+                          T* Ke, int64_t t0, int64_t t1, cudaStream_t s) {
+  if (t1 <= t0) return;
+  int64_t blocks = (t1 - t0 + JAC_TETS_PER_BLOCK - 1) / JAC_TETS_PER_BLOCK;
   if (blocks > 152 * 256) blocks = 152 * 256;
-  k_elem_jacobian<T><<<(int)blocks, 28 * JAC_TETS_PER_BLOCK, 0, s>>>(m, mc, Xl, y, y1, y2, Ke);
+  k_elem_jacobian<T><<<(int)blocks, 28 * JAC_TETS_PER_BLOCK, 0, s>>>(m, mc, Xl, y, y1, y2, Ke, t0, t1);
 }
 
 void launch_states_to_float(int64_t n, const double* a, const double* b, const double* c, float* out,
@@ -313,8 +324,8 @@ void launch_states_to_float(int64_t n, const double* a, const double* b, const d
 
 template <class T>
 void launch_gather_jacobian(int64_t nnzb, const int64_t* bptr, const int32_t* bsrc, const T* Ke, T* vals,
-                            cudaStream_t s) {
-  k_gather_jacobian<T><<<grid_for(49 * nnzb, 256), 256, 0, s>>>(nnzb, bptr, bsrc, Ke, vals);
+                            int64_t t0, int64_t t1, cudaStream_t s) {
+  k_gather_jacobian<T><<<grid_for(49 * nnzb, 256), 256, 0, s>>>(nnzb, bptr, bsrc, Ke, vals, t0, t1);
 }
 
 template <class T>
@@ -324,13 +335,13 @@ void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int3
 }
 
 template void launch_elem_jacobian<double>(const MeshDev&, const MatConst&, const double*, const double*,
-                                           const double*, const double*, double*, cudaStream_t);
+                                           const double*, const double*, double*, int64_t, int64_t, cudaStream_t);
 template void launch_elem_jacobian<float>(const MeshDev&, const MatConst&, const float*, const float*,
-                                          const float*, const float*, float*, cudaStream_t);
+                                          const float*, const float*, float*, int64_t, int64_t, cudaStream_t);
 template void launch_gather_jacobian<double>(int64_t, const int64_t*, const int32_t*, const double*, double*,
-                                             cudaStream_t);
+                                             int64_t, int64_t, cudaStream_t);
 template void launch_gather_jacobian<float>(int64_t, const int64_t*, const int32_t*, const float*, float*,
-                                            cudaStream_t);
+                                            int64_t, int64_t, cudaStream_t);
 template void launch_constraint_jacobian<double>(const MeshDev&, const MatConst&, const int32_t*, double*,
                                                  cudaStream_t);
 template void launch_constraint_jacobian<float>(const MeshDev&, const MatConst&, const int32_t*, float*,

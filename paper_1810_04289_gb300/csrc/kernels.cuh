@@ -34,15 +34,18 @@ void launch_constraint_residual(const MeshDev& m, const MatConst& mc, double t, 
                                 const double* y1, double* F, cudaStream_t s);
 // Xl: per-tet reference coordinates relative to vertex 0 (12 per tet); y, y1, y2
 // node states, all in the arithmetic type T
+// element Jacobians of the tets [t0, t1) into Ke (784 values per tet, from tet t0)
 template <class T>
 void launch_elem_jacobian(const MeshDev& m, const MatConst& mc, const T* Xl, const T* y, const T* y1, const T* y2,
-                          T* Ke, cudaStream_t s);
+                          T* Ke, int64_t t0, int64_t t1, cudaStream_t s);
 // out = [a | b | c] converted to FP32 (3 n floats)
 void launch_states_to_float(int64_t n, const double* a, const double* b, const double* c, float* out,
                             cudaStream_t s);
+// add the element blocks of the tets [t0, t1) (Ke as above) into the BSR values;
+// t0 = 0 starts the sums
 template <class T>
 void launch_gather_jacobian(int64_t nnzb, const int64_t* bptr, const int32_t* bsrc, const T* Ke, T* vals,
-                            cudaStream_t s);
+                            int64_t t0, int64_t t1, cudaStream_t s);
 template <class T>
 void launch_constraint_jacobian(const MeshDev& m, const MatConst& mc, const int32_t* diag, T* vals,
                                 cudaStream_t s);
@@ -127,6 +130,7 @@ struct RasStreamDev {
   const int64_t* item_row;  // [items] end row of each item (subdomain-relative)
   const int32_t* item_blk;  // [items][4] first / end block of the item in the subdomain's L and U streams
   int32_t max_depth;        // deepest D (the CTA has 2^max_depth warps)
+  int32_t pair;             // 1: paired-warp kernel (no dissection; SB and NST powers of two)
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);

@@ -50,7 +50,8 @@ class FsiOptions(ctypes.Structure):
                 ("jac_lag", ctypes.c_int32), ("ilu_level", ctypes.c_int32), ("threads_per_row", ctypes.c_int32),
                 ("ordering", ctypes.c_int32), ("factor_mode", ctypes.c_int32),
                 ("verbose", ctypes.c_int32), ("fault_test", ctypes.c_int32), ("apply_mode", ctypes.c_int32),
-                ("stage_blocks", ctypes.c_int32), ("stages", ctypes.c_int32), ("orth", ctypes.c_int32)]
+                ("stage_blocks", ctypes.c_int32), ("stages", ctypes.c_int32), ("orth", ctypes.c_int32),
+                ("jac_chunk", ctypes.c_int32)]
 
 
 class FsiSolveStats(ctypes.Structure):

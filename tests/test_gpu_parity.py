@@ -253,3 +253,19 @@ def test_newton_steps_with_selective_reorthogonalisation_match_oracle(tube0, ora
         rel = rel_by_group(y, ref[k])
         assert st.converged == 1
         assert all(v < tol for v in rel.values()), (k, rel)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_chunked_jacobian_assembly_is_bitwise_identical(tube0, precision):
+    """The element Jacobians assembled in chunks of tets (jac_chunk; the default
+    chunk holds what the factor storage holds) sum into the same BSR values in the
+    same order: the matrices are equal bit for bit."""
+    y, y1, y2 = perturbed_states(tube0, 90)
+    mats = []
+    for chunk in (0, 97, 1000):
+        S = make_solver(tube0, precision=precision, jac_chunk=chunk)
+        S.set_state(y1, y2, None, t=0.25)
+        S.jacobian(y)
+        mats.append(fsi.fsi_jacobian_export(S.ctx)[2])
+        S.close()
+    assert np.array_equal(mats[0], mats[1]) and np.array_equal(mats[0], mats[2])
