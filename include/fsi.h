@@ -143,11 +143,8 @@ typedef struct {
   int32_t apply_mode;     /* preconditioner apply kernel: 0 automatic (the streamed
                              apply when its shared-memory footprint fits, else the
                              level-scheduled one); 1 streamed (FSI_ERR_ARG if it does
-                             not fit); 2 level-scheduled; 3 streamed with one warp per
-                             nested-dissection part even for undissected subdomains
-                             (one warp per subdomain; otherwise, for orderings 0-2, two
-                             warps share each subdomain's rows). Same arithmetic, same
-                             result up to the order of the row sums. */
+                             not fit); 2 level-scheduled. Same arithmetic, same result
+                             up to the order of the row sums. */
   int32_t stage_blocks;   /* streamed apply: factor blocks per ring stage, 0 = automatic
                              (sized so that every subdomain's CTA is resident) */
   int32_t stages;         /* streamed apply: ring stages in flight per warp, 2..8,
@@ -195,9 +192,7 @@ typedef struct {
   int64_t device_bytes;        /* device memory held by the context */
   int64_t n_wss_faces;         /* inner-wall faces (fluid tet against wall tet) */
   int32_t nd_depth;            /* deepest nested dissection of a subdomain (ordering 3), else 0 */
-  int32_t apply_kernel;        /* preconditioner apply in use: 1 streamed, two warps per
-                                  subdomain; 2 level-scheduled; 3 streamed, one warp per
-                                  nested-dissection part */
+  int32_t apply_kernel;        /* preconditioner apply in use: 1 streamed, 2 level-scheduled */
 } fsi_info;
 
 /* Defaults: dt 1e-3, newton_rtol 1e-6, newton_atol 1e-10, gmres_rtol 1e-3,

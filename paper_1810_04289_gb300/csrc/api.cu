@@ -568,7 +568,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     }
     if (o.jac_chunk < 0) throw StatusError{FSI_ERR_ARG, "jac_chunk must be >= 0"};
     if (o.orth != 0 && o.orth != 1) throw StatusError{FSI_ERR_ARG, "orth must be 0 or 1"};
-    if (o.apply_mode < 0 || o.apply_mode > 3) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0..3"};
+    if (o.apply_mode < 0 || o.apply_mode > 2) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0, 1 or 2"};
     if (o.stage_blocks < 0) throw StatusError{FSI_ERR_ARG, "stage_blocks must be >= 0"};
     if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) throw StatusError{FSI_ERR_ARG, "stages must be 0 or 2..8"};
     if (o.precision != 0 && o.precision != 1) throw StatusError{FSI_ERR_ARG, "precision must be 0 or 1"};
@@ -985,33 +985,13 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       SB = std::max<int64_t>(W > 1 ? 8 : 16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
       if (o.stage_blocks > 0) SB = o.stage_blocks;
       (void)maxblk;
-      rs.pair = (R.max_depth == 0 && o.apply_mode != 3) ? 1 : 0;
-      if (rs.pair) {
-        // paired-warp kernel: NST stages of SB blocks, both powers of two, a row
-        // spanning at most NST stages ((NST - 1) SB + 1 >= the longest row part);
-        // SB as large as the shared memory left per CTA allows (every CTA resident)
-        const int64_t pfixed = 256 + 8 * R.max_rows * vsz + 8 * (R.max_rows + 1) + 16 + 1024;
-        const int64_t pbudget = std::min<int64_t>((int64_t)(227 * 1024) / per_sm, (int64_t)(200 * 1024));
-        nst = o.stages > 0 ? o.stages : 4;
-        if (nst & (nst - 1)) throw StatusError{FSI_ERR_ARG, "stages must be a power of two for this apply"};
-        SB = 8;
-        while (SB * 2 * nst * stride * vsz + pfixed <= pbudget && SB < (cp->mixed ? 64 : 32)) SB *= 2;
-        if (o.stage_blocks > 0) {
-          SB = o.stage_blocks;
-          if (SB & (SB - 1)) throw StatusError{FSI_ERR_ARG, "stage_blocks must be a power of two for this apply"};
-        }
-        while ((nst - 1) * SB + 1 < maxblk) {
-          if (o.stages == 0 && nst < 8) nst *= 2;
-          else SB *= 2;
-        }
-      }
       rs.nst = nst;
       rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
       const bool fits = sm <= 200 * 1024;
-      if ((o.apply_mode == 1 || o.apply_mode == 3) && !fits)
+      if (o.apply_mode == 1 && !fits)
         throw StatusError{FSI_ERR_ARG, "apply_mode 1: the streamed apply's shared memory does not fit"};
       cp->use_stream = o.apply_mode == 2 ? false : fits;
       if (cp->use_stream) {
@@ -1304,7 +1284,7 @@ fsi_status fsi_get_info(const fsi_ctx* c, fsi_info* info) {
   info->device_bytes = c->dev_bytes;
   info->n_wss_faces = c->nwss;
   info->nd_depth = c->plan.max_depth;
-  info->apply_kernel = c->use_stream ? (c->rs.pair ? 1 : 3) : 2;
+  info->apply_kernel = c->use_stream ? 1 : 2;
   return FSI_OK;
 }
 

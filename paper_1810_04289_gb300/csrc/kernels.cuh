@@ -130,7 +130,6 @@ struct RasStreamDev {
   const int64_t* item_row;  // [items] end row of each item (subdomain-relative)
   const int32_t* item_blk;  // [items][4] first / end block of the item in the subdomain's L and U streams
   int32_t max_depth;        // deepest D (the CTA has 2^max_depth warps)
-  int32_t pair;             // 1: paired-warp kernel (no dissection; SB and NST powers of two)
 };
 template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r);

@@ -382,268 +382,6 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Paired-warp streamed RAS apply (Sec. 3, Eq. 16) for subdomains solved as one
-// sequence of rows (orderings 0-2): one CTA of three warps per subdomain. Warp 2
-// (one lane) streams the packed factor blocks into a ring of NST stages of SB
-// blocks (cp.async.bulk, mbarrier completion, SB and NST powers of two); warps 0
-// and 1 solve the rows alternately (warp q mod 2 takes row q). Row q of the
-// forward solve needs every earlier row, but all rows up to q - 2 are finished
-// when its warp starts it, so the warp sums every block except the one in column
-// q - 1 at once, then waits for the other warp to finish row q - 1 (a named
-// barrier: the finishing warp arrives, the waiting one syncs) and adds that
-// block last; only one block's product lies on the chain from row to row. The
-// backward solve runs the rows in decreasing order the same way (its dependent
-// block is the one in column q + 1). Each consumer waits for every stage
-// (full barrier) and hands every stage back (empty barrier, two arrivals) once
-// its rows no longer need it. All waits on stages are bounded; a wait that gives
-// up raises a shared abort flag, after which every warp only keeps the named
-// barriers paired until the end, records FSI_ERR_TIMEOUT-style status in *err
-// and lets the copies in flight land (bounded).
-// ---------------------------------------------------------------------------
-
-// per-lane partial of sum over blocks [pb, pe) of a stream of (block, row c) .
-// w[col(block)]; stream block p sits in ring slot (rbase + p) & rmask (the ring
-// is NST * SB blocks, a power of two; rbase = the stream's first stage times SB).
-// Lane 7 j + c takes blocks pb + j, pb + j + 4, ...
-template <class TF, int STR>
-__device__ __forceinline__ TF pair_part(const TF* ring, int rbase, int rmask, int pb, int pe, const TF* w, int j,
-                                        int c) {
-  TF acc = TF(0);
-  if (j < 4) {
-    for (int b = pb + j; b < pe; b += 16) {
-      int cols[4];
-      const TF* blk[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int bi = b + 4 * i < pe ? b + 4 * i : b;
-        blk[i] = ring + (size_t)((rbase + bi) & rmask) * STR;
-        cols[i] = b + 4 * i < pe ? blk_col(blk[i]) : -1;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (cols[i] >= 0) acc += row7(blk[i] + 8 * c, w + 8 * cols[i]);
-    }
-  }
-  return acc;
-}
-
-// bounded wait with a suspend-time hint (the waiting lane may sleep up to about
-// hint_ns per try); gives up after 2^20 tries or when *abort is raised (checked
-// every 256 tries)
-__device__ __forceinline__ bool mbar_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns,
-                                               volatile int* abort) {
-  for (uint32_t it = 0; it < (1u << 20); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    if (ok) return true;
-    if ((it & 255) == 255 && *abort) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void named_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
-__device__ __forceinline__ void named_arrive(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
-
-template <class TF>
-__global__ void __launch_bounds__(96) k_ras_apply_pair(RasStreamDev R, const double* __restrict__ rin,
-                                                       double* __restrict__ z, float* __restrict__ z32, int32_t* err,
-                                                       const int* __restrict__ guard) {
-  if (guard && *guard == 0) return;
-  constexpr int STR = Pack<TF>::stride;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int NST = R.nst, SB = R.stage_blocks;
-  const int sbs = __ffs(SB) - 1, nstm = NST - 1;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* empty = full + NSTMAX;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTMAX);
-  TF* ring = reinterpret_cast<TF*>(smem + 256);
-  TF* w = ring + (size_t)NST * SB * STR;
-  int* Lptr = reinterpret_cast<int*>(w + 8 * (size_t)R.max_rows);  // [m+1] first L block of each row
-  int* Uptr = Lptr + R.max_rows + 1;                                // [m+1] first U block of each row (rows descending)
-  const int s = blockIdx.x;
-  const int64_t r0 = R.sd_row[s];
-  const int m = (int)(R.sd_row[s + 1] - r0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t Lb0 = R.L_off[s], Ub0 = R.U_off[s];
-  const int nLb = (int)(R.L_off[s + 1] - Lb0), nUb = (int)(R.U_off[s + 1] - Ub0);
-  const int nGL = (nLb + SB - 1) >> sbs, nGU = (nUb + SB - 1) >> sbs;
-  const TF* Lpack = reinterpret_cast<const TF*>(R.Lpack) + (size_t)Lb0 * STR;
-  const TF* Upack = reinterpret_cast<const TF*>(R.Upack) + (size_t)Ub0 * STR;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < NST; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 2);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // restriction R_i^delta r into shared memory, 8-wide rows
-  for (int q = threadIdx.x; q < m; q += blockDim.x) {
-    const double* src = rin + 7 * (int64_t)R.gnode[r0 + q];
-    double v[7];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) v[c] = src[c];
-#pragma unroll
-    for (int c = 0; c < 7; ++c) w[8 * q + c] = (TF)v[c];
-    w[8 * q + 7] = TF(0);
-  }
-  // block offsets of the rows in the two streams (warp 0: prefix sums)
-  if (warp == 0) {
-    int accL = 0, accU = 0;
-    for (int base = 0; base < m; base += 32) {
-      const int q = base + lane;
-      int vL = q < m ? (int)R.L_cnt[r0 + q] : 0;
-      int vU = (m - 1 - q) >= 0 && q < m ? (int)R.U_cnt[r0 + (m - 1 - q)] : 0;   // U stream: rows descending
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int tL = __shfl_up_sync(0xffffffffu, vL, o), tU = __shfl_up_sync(0xffffffffu, vU, o);
-        if (lane >= o) vL += tL, vU += tU;
-      }
-      if (q < m) {
-        Lptr[q + 1] = accL + vL;
-        Uptr[m - 1 - q] = accU + vU;   // position after row (m-1-q) in the U stream = start of row m-2-q
-      }
-      accL += __shfl_sync(0xffffffffu, vL, 31);
-      accU += __shfl_sync(0xffffffffu, vU, 31);
-    }
-    if (lane == 0) {
-      Lptr[0] = 0;
-      Uptr[m] = 0;   // row m (none) ends where the U stream begins
-    }
-  }
-  __syncthreads();
-  // Uptr[q] now holds the end of row q in the U stream (rows descending: row q
-  // occupies [Uptr[q+1], Uptr[q]))
-
-  if (warp == 2) {
-    if (lane == 0) {
-      const int ngroups = nGL + nGU;
-      bool ok = true;
-      int it = 0;
-      for (; it < ngroups && !R.stall; ++it) {
-        const int st = it & nstm;
-        if (it >= NST) ok = mbar_wait_hint(&empty[st], ((it / NST) - 1) & 1, 2000, abort_flag);
-        if (!ok || *abort_flag) {
-          ok = false;
-          break;
-        }
-        const bool isL = it < nGL;
-        const int first = (isL ? it : it - nGL) << sbs;
-        const int nb = min(SB, (isL ? nLb : nUb) - first);
-        const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
-        mbar_arrive_expect_tx(&full[st], bytes);
-        bulk_g2s(ring + ((size_t)st << sbs) * STR, (isL ? Lpack : Upack) + (size_t)first * STR, bytes, &full[st]);
-      }
-      if (!ok) *abort_flag = 1;
-      for (int k = (it > NST ? it - NST : 0); k < it; ++k) mbar_wait(&full[k & nstm], (k / NST) & 1);
-    }
-    return;
-  }
-
-  // consumers
-  const int j = lane / 7, c = lane - 7 * (lane / 7);
-  const int me = warp, other = 1 - warp;
-  int waited = 0, released = 0;  // stages (in stream order: L then U) waited for / handed back by this warp
-  const int rmask = NST * SB - 1;
-  auto wait_upto = [&](int k_end) {  // wait for stages [waited, k_end)
-    for (; waited < k_end; ++waited) {
-      if (*abort_flag) continue;
-      if (!mbar_wait_hint(&full[waited & nstm], (waited / NST) & 1, 200, abort_flag)) *abort_flag = 1;
-    }
-  };
-  // hand back stages [released, k_end), in order; a stage this warp never read
-  // is waited for first (its fill must have landed, so that the two warps' hand
-  // backs of one ring slot always belong to the same fill), one stage at a time
-  // (a stage further on may need this warp's earlier hand backs to be filled)
-  auto release_upto = [&](int k_end) {
-    __syncwarp();
-    for (int k = released; k < k_end; ++k) {
-      if (k >= waited) wait_upto(k + 1);
-      if (lane == 0) mbar_arrive(&empty[k & nstm]);
-    }
-    released = k_end > released ? k_end : released;
-  };
-
-  // forward solve: w_q -= sum_k L_qk w_k, rows ascending, row q on warp q mod 2
-  for (int q = me; q < m; q += 2) {
-    const int pb = Lptr[q], pe = Lptr[q + 1];
-    const int nb = pe - pb;
-    if (nb > 0) wait_upto((pe - 1 + SB) >> sbs);
-    TF acc = TF(0);
-    const TF* dblk = ring + (size_t)((pe - 1) & rmask) * STR;  // the row's last block
-    int dcol = -1;  // its column, when it is q - 1 (the other warp's row)
-    if (!*abort_flag) {
-      if (nb > 0 && q > 0 && blk_col(dblk) == q - 1) dcol = q - 1;
-      acc = pair_part<TF, STR>(ring, 0, rmask, pb, pe - (dcol >= 0 ? 1 : 0), w, j, c);
-    }
-    if (q > 0) named_sync(1 + other);
-    if (dcol >= 0 && j == 0 && !*abort_flag) acc += row7(dblk + 8 * c, w + 8 * dcol);
-    acc += __shfl_down_sync(0xffffffffu, acc, 14);
-    acc += __shfl_down_sync(0xffffffffu, acc, 7);
-    if (lane < 7) w[8 * q + lane] -= acc;
-    __syncwarp();
-    if (q + 1 < m) named_arrive(1 + me);
-    // stages wholly before this warp's next row are no longer needed by it
-    const int nxt = q + 2 < m ? Lptr[q + 2] : nLb;
-    release_upto(q + 2 < m ? (nxt >> sbs) : nGL);
-  }
-  if (me >= m) release_upto(nGL);  // a warp without rows still hands the L stages back
-  named_sync(3);                   // both forward halves done before any backward row
-  // backward solve: w_q = D_q^{-1} w_q + sum_j (-D_q^{-1} U_qj) w_j, rows descending,
-  // row q on warp (m - 1 - q) mod 2; row q's blocks are [Uptr[q+1], Uptr[q]) of
-  // the U stream, the inverted pivot first, then the columns in increasing order
-  for (int t = me; t < m; t += 2) {
-    const int q = m - 1 - t;
-    const int pb = Uptr[q + 1], pe = Uptr[q];
-    const int nb = pe - pb;
-    wait_upto(nGL + ((pe - 1 + SB) >> sbs));
-    TF acc = TF(0);
-    const int ub = nGL << sbs;  // ring base of the U stream
-    const TF* dblk = ring + (size_t)((ub + pb + 1) & rmask) * STR;  // the row's second block
-    int dcol = -1;  // its column, when it is q + 1 (the other warp's row)
-    if (!*abort_flag) {
-      if (nb > 1 && t > 0 && blk_col(dblk) == q + 1) dcol = q + 1;
-      // the inverted pivot (column q, times the forward result in w_q), then the
-      // blocks after the dependent one
-      acc = pair_part<TF, STR>(ring, ub, rmask, pb, pb + 1, w, j, c);
-      acc += pair_part<TF, STR>(ring, ub, rmask, pb + 1 + (dcol >= 0 ? 1 : 0), pe, w, j, c);
-    }
-    if (t > 0) named_sync(1 + other);
-    if (dcol >= 0 && j == 0 && !*abort_flag) acc += row7(dblk + 8 * c, w + 8 * dcol);
-    acc += __shfl_down_sync(0xffffffffu, acc, 14);
-    acc += __shfl_down_sync(0xffffffffu, acc, 7);
-    if (lane < 7) w[8 * q + lane] = acc;
-    __syncwarp();
-    if (t + 1 < m) named_arrive(1 + me);
-    const int nxt = t + 2 < m ? Uptr[m - 1 - (t + 2) + 1] : nUb;   // start of this warp's next row
-    release_upto(nGL + (t + 2 < m ? (nxt >> sbs) : nGU));
-  }
-  if (me >= m) release_upto(nGL + nGU);
-  named_sync(3);
-  if (*abort_flag) {
-    if (threadIdx.x == 0) atomicExch(err, 2);
-    return;
-  }
-  // restricted prolongation (R_i^0)^T: owned rows only (the two consumer warps)
-  for (int q = threadIdx.x; q < m; q += 64) {
-    if (R.owned[r0 + q]) {
-      const int64_t g7 = 7 * (int64_t)R.gnode[r0 + q];
-#pragma unroll
-      for (int cc = 0; cc < 7; ++cc) z[g7 + cc] = (double)w[8 * q + cc];
-      if (z32) {
-#pragma unroll
-        for (int cc = 0; cc < 7; ++cc) z32[g7 + cc] = (float)w[8 * q + cc];
-      }
-    }
-  }
-}
-
 // copy the factor blocks into the packed streams (7 rows of 8: the row's 7
 // entries, then the column index in row 0's last slot, zeros in the others); a
 // U block with a pivot (Upiv >= 0) is stored as -D_q^{-1} U_qj, the row's
@@ -690,14 +428,7 @@ __global__ void k_pack_factors(int64_t nL, const int64_t* __restrict__ Lsrc, con
 }  // namespace
 
 template <class TF>
-size_t ras_pair_smem(const RasStreamDev& r) {
-  return 256 + (size_t)r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) + (size_t)8 * r.max_rows * sizeof(TF) +
-         (size_t)8 * (r.max_rows + 1) + 16;
-}
-
-template <class TF>
 size_t ras_stream_smem(const RasStreamDev& r) {
-  if (r.pair) return ras_pair_smem<TF>(r);
   const size_t W = (size_t)1 << r.max_depth;
   return 128 * ((W * NSTMAX * 8 + 127) / 128) + W * r.nst * r.stage_blocks * Pack<TF>::stride * sizeof(TF) +
          (size_t)8 * r.max_rows * sizeof(TF) + (size_t)4 * r.max_rows + 16;
@@ -714,13 +445,6 @@ void launch_pack_factors(const RasStreamDev& r, const TF* fac, cudaStream_t s) {
 
 template <class TF>
 cudaError_t ras_stream_init(const RasStreamDev& r) {
-  if (r.pair) {
-    cudaError_t e = cudaFuncSetAttribute(k_ras_apply_pair<TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_ras_apply_pair<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ras_pair_smem<TF>(r));
-  }
   // all of the unified L1/shared storage as shared memory: several CTAs per SM
   cudaError_t e = cudaFuncSetAttribute(k_ras_apply_stream<TF>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                        (int)cudaSharedmemCarveoutMaxShared);
@@ -732,10 +456,7 @@ cudaError_t ras_stream_init(const RasStreamDev& r) {
 template <class TF>
 cudaError_t launch_ras_apply_stream(const RasStreamDev& r, const double* rin, double* z, float* z32, int32_t* err,
                                     const int* guard, cudaStream_t s) {
-  if (r.pair)
-    k_ras_apply_pair<TF><<<r.np, 96, ras_pair_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
-  else
-    k_ras_apply_stream<TF><<<r.np, 32 << r.max_depth, ras_stream_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
+  k_ras_apply_stream<TF><<<r.np, 32 << r.max_depth, ras_stream_smem<TF>(r), s>>>(r, rin, z, z32, err, guard);
   return cudaGetLastError();
 }
 

@@ -142,7 +142,7 @@ def test_level_scheduled_apply_matches_oracle(case, precision, ilu, nsub, orderi
                        apply_mode=1)
     zl, i2 = gpu_apply(m, y, y0, r, precision=precision, n_subdomains=nsub, ilu_level=ilu, ordering=ordering,
                        apply_mode=2)
-    assert i1.apply_kernel == (3 if ordering == 3 else 1) and i2.apply_kernel == 2
+    assert i1.apply_kernel == 1 and i2.apply_kernel == 2
     tol = tolerance(m, J, r, zo, nsub, ilu, ordering, fp32=precision == 1)
     for z in (zs, zl):
         rel = rel_by_group(z, zo)
@@ -172,18 +172,3 @@ def test_bilu0_one_subdomain_on_a_rigid_tube_is_not_exact_but_ilu_full_is(case):
         zg, _ = gpu_apply(m, y, y0, r, n_subdomains=1, ilu_level=ilu)
         res.append(np.linalg.norm(r.reshape(-1) - J @ zg.reshape(-1)))
     assert res[2] < res[1] < res[0], res
-
-
-@pytest.mark.parametrize("precision,ilu,nsub", [(0, 1, 4), (0, 2, 64), (1, 1, 4)])
-def test_one_warp_streamed_apply_matches_oracle(case, precision, ilu, nsub):
-    """apply_mode 3 runs undissected subdomains through the one-warp-per-part
-    streamed kernel instead of the two-warp one; both equal the oracle's apply."""
-    m, y, y0, J, r = case
-    zo, _ = oracle_apply(m, J, r, nsub, ilu, 1)
-    z1, i1 = gpu_apply(m, y, y0, r, precision=precision, n_subdomains=nsub, ilu_level=ilu, apply_mode=3)
-    z2, i2 = gpu_apply(m, y, y0, r, precision=precision, n_subdomains=nsub, ilu_level=ilu, apply_mode=1)
-    assert i1.apply_kernel == 3 and i2.apply_kernel == 1
-    tol = tolerance(m, J, r, zo, nsub, ilu, 1, fp32=precision == 1)
-    for z in (z1, z2):
-        rel = rel_by_group(z, zo)
-        assert within(rel, tol), (rel, tol)
