@@ -57,6 +57,17 @@ TUNED = {
                                  jac_lag=3),
     ("tree-3gen", "fp64"): dict(n_subdomains=16384, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                 jac_lag=3),
+    # 7-generation tree (43.0 M unknowns): subdomains of the same size as on the
+    # 3-generation tree (about 150 owned nodes each)
+    ("tree-7gen", "mixed"): dict(n_subdomains=49152, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                 jac_lag=3),
+    ("tree-7gen", "fp64"): dict(n_subdomains=49152, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                jac_lag=3),
+    # the same tree at h = 0.08 (2.09 M unknowns): subdomains of the same size
+    ("tree-3gen-h08", "mixed"): dict(n_subdomains=2048, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                     jac_lag=3),
+    ("tree-3gen-h08", "fp64"): dict(n_subdomains=2048, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+                                    jac_lag=3),
     ("tube-96x32x15", "mixed"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                      jac_lag=3),
     ("tube-96x32x15", "fp64"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
@@ -65,7 +76,9 @@ TUNED = {
 # DRAM bytes per launch (read + write) from one ncu capture of the kernel as it is
 # now, keyed by (workload, phase, precision, subdomains, ILU level, ordering);
 # the summary that holds the capture is named beside it
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("tree-3gen", "pcapply", "mixed", 16384, 1, 1): (27.41e9, "profiles/k_ras_apply_stream_tree-3gen.md"),
+}
 
 
 def parse():
@@ -90,6 +103,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--autotune", action="store_true", help="search the options instead of the committed ones")
+    p.add_argument("--kernels-only", type=int, default=0, metavar="R",
+                   help="profiling aid: build the headline-precision solver for the workload, assemble the "
+                        "Jacobian at the workload's initial state without the Stokes solve (rest for trees), "
+                        "then time R preconditioner applies and R SpMVs and print their mean times")
     return p.parse_args()
 
 
@@ -448,8 +465,45 @@ def cpu_sample(args, m, steps_hint=None, all_cores=True, per_core_tets=None):
                        f"(assembly-only, an upper bound on the oracle's steps/s)")}
 
 
+def kernels_only(args):
+    """R applies and R SpMVs of the headline-precision solver (see --kernels-only)."""
+    import torch
+    from paper_1810_04289_gb300 import fsi
+    import vesselmesh as vm
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    m = make_mesh(args.workload)
+    prec = args.precisions.split(",")[0]
+    opt, _ = options_for(args, prec, fsi)
+    kinds = [q.get("kind") for q in m.info.get("problems", [m.info])]
+    y0 = vm.poiseuille_state(m) if all(k == "tube" for k in kinds) else np.zeros((m.n_nodes, 7))
+    S = fsi.Solver(m, MATERIAL, opt)
+    S.set_state(y0, t=0.0)
+    fsi.fsi_jacobian(S.ctx, S.vec(y0))
+    r = torch.randn((m.n_nodes, 7), dtype=torch.float64, device="cuda")
+    z = S.vec()
+    out = {}
+    for name, fn in (("pcapply", lambda: fsi.fsi_pc_apply(S.ctx, r, z)), ("spmv", lambda: fsi.fsi_spmv(S.ctx, r, z))):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.kernels_only):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = a.elapsed_time(b) / args.kernels_only
+    info = S.info()
+    out.update(workload=args.workload, precision=prec, factor_blocks=info.factor_blocks, factor_rows=info.factor_rows,
+               nnzb=info.nnzb, subdomains=info.n_subdomains, apply_kernel=info.apply_kernel)
+    S.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.kernels_only > 0:
+        kernels_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -100,13 +100,22 @@ __global__ void k_seg_maxpy(SegDev sg, int64_t n, int32_t nv, const double* __re
   }
 }
 
-// y_i = x_i / scal[p(i) * lds] (0 where the scale is 0)
+// y_i = x_i / scal[p(i) * lds] (0 where the scale is 0). The reciprocal is
+// formed once per problem a thread meets (consecutive elements of a thread
+// mostly share their problem), not once per element: y_i = x_i * (1 / a).
 __global__ void k_seg_scale_inv(SegDev sg, int64_t n, const double* __restrict__ x, const double* __restrict__ scal,
                                 int32_t lds, double* __restrict__ y, const int* guard) {
   if (off(guard)) return;
+  int pc = -1;
+  double inv = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = scal[(int64_t)sg.node_prob[i / 7] * lds];
-    y[i] = a != 0.0 ? x[i] / a : 0.0;
+    const int p = sg.node_prob[i / 7];
+    if (p != pc) {
+      const double a = scal[(int64_t)p * lds];
+      inv = a != 0.0 ? 1.0 / a : 0.0;
+      pc = p;
+    }
+    y[i] = x[i] * inv;
   }
 }
 
