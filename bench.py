@@ -93,6 +93,8 @@ def parse():
     p.add_argument("--overlap", type=int, default=None)
     p.add_argument("--ordering", type=int, default=None)
     p.add_argument("--jac-lag", type=int, default=None)
+    p.add_argument("--orth", type=int, default=None,
+                   help="Gram-Schmidt form (fsi_options.orth); default the library's (0)")
     p.add_argument("--newton-rtol", type=float, default=1e-6)
     p.add_argument("--gmres-rtol", type=float, default=1e-3)
     p.add_argument("--precisions", default="mixed,fp64")
@@ -236,7 +238,7 @@ def options_for(args, prec, fsi):
     base = dict(n_subdomains=256, overlap=1, ilu_level=1, ordering=1, threads_per_row=32, jac_lag=1)
     base.update(TUNED.get((args.workload, prec), {}))
     for k, a in (("n_subdomains", args.subdomains), ("ilu_level", args.ilu), ("overlap", args.overlap),
-                 ("ordering", args.ordering), ("jac_lag", args.jac_lag)):
+                 ("ordering", args.ordering), ("jac_lag", args.jac_lag), ("orth", args.orth)):
         if a is not None:
             base[k] = a
     return fsi.fsi_default_options(newton_rtol=args.newton_rtol, gmres_rtol=args.gmres_rtol, precision=pflag,
@@ -276,10 +278,10 @@ def run_ours(args, rank, world):
             opt, table = autotune(m, MATERIAL, y0, base=opt)
             opt, lag_table = tune_jac_lag(m, MATERIAL, y0, opt)
             tuned = {"chosen": {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level", "ordering",
-                                                             "threads_per_row", "jac_lag")},
+                                                             "threads_per_row", "jac_lag", "orth")},
                      "seconds": time.perf_counter() - t_tune, "candidates": table, "jac_lag": lag_table}
         chosen = {k: getattr(opt, k) for k in ("n_subdomains", "overlap", "ilu_level", "ordering",
-                                               "threads_per_row", "jac_lag")}
+                                               "threads_per_row", "jac_lag", "orth")}
         t0 = time.perf_counter()
         S = fsi.Solver(m, MATERIAL, opt)
         t_create = time.perf_counter() - t0
@@ -567,7 +569,8 @@ def main():
         "config": {"workload": args.workload, "nodes": hi["n_nodes"], "unknowns": hi["n_unknowns"],
                    "tets": hi["n_tets"], "subdomains": hi["n_subdomains"], "overlap": ch["overlap"],
                    "ilu": ch["ilu_level"], "ordering": ch["ordering"], "jac_lag": ch["jac_lag"],
-                   "threads_per_row": ch["threads_per_row"],
+                   "threads_per_row": ch["threads_per_row"], "orth": ch["orth"],
+                   "device_gb": round(hi["device_bytes"] / 1e9, 2), "factor_blocks": hi["factor_blocks"],
                    "options": "committed tuned choice" if head["committed"] and not args.autotune else
                    ("autotuned in this run" if args.autotune else "defaults / flags"),
                    "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol,

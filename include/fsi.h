@@ -139,7 +139,9 @@ typedef struct {
   int32_t verbose;        /* print per-iteration norms to stderr */
   int32_t fault_test;     /* tests only: 1 = the preconditioner apply's copy engine
                              issues nothing, so the apply's bounded wait runs out and
-                             the call returns FSI_ERR_TIMEOUT; 0 otherwise */
+                             the call returns FSI_ERR_TIMEOUT; 2 = Gram-Schmidt orth 0
+                             forms every new vector's norm from the updated vector (its
+                             fallback path); 0 otherwise */
   int32_t apply_mode;     /* preconditioner apply kernel: 0 automatic (the streamed
                              apply when its shared-memory footprint fits, else the
                              level-scheduled one); 1 streamed (FSI_ERR_ARG if it does
@@ -149,10 +151,15 @@ typedef struct {
                              (sized so that every subdomain's CTA is resident) */
   int32_t stages;         /* streamed apply: ring stages in flight per warp, 2..8,
                              0 = automatic (3) */
-  int32_t orth;           /* Arnoldi orthogonalisation: 0 classical Gram-Schmidt twice;
-                             1 classical Gram-Schmidt with a second pass only where the
-                             first removed more than 1 - 1/sqrt(2) of the vector's norm
-                             (selective reorthogonalisation) */
+  int32_t orth;           /* Arnoldi orthogonalisation, FP64 (Sec. 4: classical
+                             Gram-Schmidt twice): 0 the new vector's norm taken from the
+                             second pass (dots; update; dots with ||w||^2; update and
+                             scaling in one sweep by 1/sqrt(||w||^2 - ||h||^2), or the
+                             vector's own norm where that subtraction would lose two bits
+                             or more); 1 a second pass only where the first removed more
+                             than 1 - 1/sqrt(2) of the vector's norm (selective
+                             reorthogonalisation); 2 dots, update, dots, update, norm,
+                             scaling as separate sweeps */
   int32_t jac_chunk;      /* tets per chunk of the Jacobian assembly's element buffer,
                              0 = automatic (as many as the factors' storage, which the
                              buffer shares, holds). Any chunking gives bitwise the same

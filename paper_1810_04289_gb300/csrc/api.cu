@@ -97,7 +97,12 @@ struct fsi_ctx {
   int* active = nullptr;         // [P] problem still iterating in the cycle
   int* kcols = nullptr;          // [P] Krylov columns built in the cycle
   int* anyact = nullptr;         // [1] some problem active (guard of the captured kernels)
-  int* reorth = nullptr;         // [1] some problem needs a second Gram-Schmidt pass (orth = 1)
+  int* reorth = nullptr;         // [1] some problem needs a second Gram-Schmidt pass (orth = 1), or
+                                 // the double-float Gram-Schmidt's norm from its updated vector
+  double* gs_inv = nullptr;      // [P] reciprocal of H[j+1][j] (orth 0)
+  double* gs_nrm = nullptr;      // [P] norms formed from the updated vector (its fallback)
+  double* gs_scal = nullptr;     // [P] their divisors
+  int* gs_unsafe = nullptr;      // [P] the norm is taken from the updated vector
   int* pmask = nullptr;          // [P] problem already converged (Newton)
   double* palpha = nullptr;      // [P] line-search step per problem
   float* zf = nullptr;           // FP32 copy of the SpMV input (mixed precision)
@@ -363,6 +368,27 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
     c->launches += 9;
     return;
   }
+  if (c->opt.orth == 0) {
+    // classical Gram-Schmidt twice, the new norm from the second pass: dots;
+    // update; dots with ||w||^2; norm = sqrt(||w||^2 - ||h2||^2); update and scale
+    // in one sweep. Where that norm is unsafe the guarded kernels form it from the
+    // updated vector.
+    double* hj = c->H + (int64_t)j * ldh + j + 1;
+    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
+    launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
+    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st, 1);
+    launch_seg_norm_pythagoras(P, c->hB, ldh, j, hj, (int64_t)ldh * m, c->gs_inv, c->gs_unsafe, c->reorth,
+                               c->opt.fault_test == 2 ? 1 : 0, guard, st);
+    launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, guard, st, c->gs_inv);
+    launch_seg_norm(c->seg, w, c->partial, c->gs_nrm, 1, c->reorth, st);
+    launch_seg_norm_fix(P, c->gs_nrm, c->gs_unsafe, hj, (int64_t)ldh * m, c->gs_scal, c->reorth, st);
+    launch_seg_scale_inv(c->seg, n, w, c->gs_scal, 1, w, c->reorth, st);
+    launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
+                      c->kcols, c->anyact, st);
+    c->launches += 9;
+    return;
+  }
+  // orth 2: dots, update, dots, update, norm, scale
   launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
   launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
@@ -567,7 +593,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       o.jac_chunk = q.jac_chunk;
     }
     if (o.jac_chunk < 0) throw StatusError{FSI_ERR_ARG, "jac_chunk must be >= 0"};
-    if (o.orth != 0 && o.orth != 1) throw StatusError{FSI_ERR_ARG, "orth must be 0 or 1"};
+    if (o.orth < 0 || o.orth > 2) throw StatusError{FSI_ERR_ARG, "orth must be 0, 1 or 2"};
     if (o.apply_mode < 0 || o.apply_mode > 2) throw StatusError{FSI_ERR_ARG, "apply_mode must be 0, 1 or 2"};
     if (o.stage_blocks < 0) throw StatusError{FSI_ERR_ARG, "stage_blocks must be >= 0"};
     if (o.stages != 0 && (o.stages < 2 || o.stages > 8)) throw StatusError{FSI_ERR_ARG, "stages must be 0 or 2..8"};
@@ -809,6 +835,10 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
     cp->kcols = cp->dalloc<int>(n_problems);
     cp->anyact = cp->dalloc<int>(1);
     cp->reorth = cp->dalloc<int>(1);
+    cp->gs_inv = cp->dalloc<double>(n_problems);
+    cp->gs_nrm = cp->dalloc<double>(n_problems);
+    cp->gs_scal = cp->dalloc<double>(n_problems);
+    cp->gs_unsafe = cp->dalloc<int>(n_problems);
     cp->pmask = cp->dalloc<int>(n_problems);
     cp->palpha = cp->dalloc<double>(n_problems);
     cp->r = cp->dalloc<double>(n);
@@ -970,10 +1000,6 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
       // shared memory per CTA leaves after the vector; the stage_blocks and
       // stages options override the choice
-      // stage geometry: NST stages of SB blocks. The subdomains should all be
-      // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
-      // shared memory per CTA leaves after the vector; the stage_blocks and
-      // stages options override the choice
       const int vsz = cp->mixed ? 4 : 8, stride = 56;  // packed block: 7 rows of 8 values
       int nst = o.stages > 0 ? o.stages : 3;
       const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
@@ -984,13 +1010,13 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       int64_t SB = (budget - fixed) / (W * nst * stride * vsz);
       SB = std::max<int64_t>(W > 1 ? 8 : 16, std::min<int64_t>(SB, cp->mixed ? 128 : 64));
       if (o.stage_blocks > 0) SB = o.stage_blocks;
-      (void)maxblk;
       rs.nst = nst;
       rs.stall = o.fault_test == 1 ? 1 : 0;
       rs.stage_blocks = (int32_t)SB;
       rs.max_rows = R.max_rows;
       const size_t sm = cp->mixed ? ras_stream_smem<float>(rs) : ras_stream_smem<double>(rs);
-      const bool fits = sm <= 200 * 1024;
+      // (the apply keeps each row's block counts as 16-bit values in shared memory)
+      const bool fits = sm <= 200 * 1024 && maxblk <= 65535;
       if (o.apply_mode == 1 && !fits)
         throw StatusError{FSI_ERR_ARG, "apply_mode 1: the streamed apply's shared memory does not fit"};
       cp->use_stream = o.apply_mode == 2 ? false : fits;

@@ -164,8 +164,14 @@ void launch_seg_reorth_decide(int32_t P, const double* ws, const double* nrm, in
                               int32_t j, const int* active, int* flag, cudaStream_t s);
 void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
                      const int* guard, cudaStream_t s);
+// w -= V h per problem, then w *= scal[p] (scal optional)
 void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,
-                      int32_t ldh, double* w, const int* guard, cudaStream_t s);
+                      int32_t ldh, double* w, const int* guard, cudaStream_t s, const double* scal = nullptr);
+// the new Arnoldi vector's norm as sqrt(||w||^2 - ||h2||^2) where that is safe (see krylov.cu)
+void launch_seg_norm_pythagoras(int32_t P, const double* hb, int32_t lda, int32_t j, double* hsub, int64_t ldsub,
+                                double* inv, int* unsafe, int* flag, int force, const int* guard, cudaStream_t s);
+void launch_seg_norm_fix(int32_t P, const double* nrm, const int* unsafe, double* hsub, int64_t ldsub, double* scal,
+                         const int* guard, cudaStream_t s);
 void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const double* scal, int32_t lds,
                           double* y, const int* guard, cudaStream_t s);
 

@@ -50,11 +50,30 @@ __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const do
 #pragma unroll
   for (int k = 0; k < MD; ++k) acc[k] = 0.0;
   const int nvv = nv - nself;  // vectors of V; the rest is w itself
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += RB) {
-    const double wi = w[i];
+  // vector k of this group: V_{k0+k} while k0 + k < nvv, else w (the self product)
+  const double* src[MD];
 #pragma unroll
-    for (int k = 0; k < MD; ++k)
-      if (k0 + k < nv) acc[k] += ((V && k0 + k < nvv) ? V[(int64_t)(k0 + k) * ldv + i] : wi) * wi;
+  for (int k = 0; k < MD; ++k) src[k] = (V && k0 + k < nvv) ? V + (int64_t)(k0 + k) * ldv : w;
+  // two elements per trip (the second predicated on the chunk's end): twice the
+  // loads in flight per thread. The kernel is bound by the FP64 pipe (one FMA per
+  // loaded operand), so only the group's live vectors take FMAs.
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += 2 * RB) {
+    const int64_t i2 = i + RB;
+    const bool two = i2 < i1;
+    const double wa = w[i], wb = two ? w[i2] : 0.0;
+    double va[MD], vb[MD];
+#pragma unroll
+    for (int k = 0; k < MD; ++k) {
+      va[k] = k0 + k < nv ? src[k][i] : 0.0;
+      vb[k] = (k0 + k < nv && two) ? src[k][i2] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < MD; ++k) {
+      if (k0 + k < nv) {
+        acc[k] += va[k] * wa;
+        acc[k] += vb[k] * wb;
+      }
+    }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -88,15 +107,17 @@ __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const do
   if (threadIdx.x == 0) *cnt = 0;
 }
 
-// w_i -= sum_k h[p(i)][k] V_k[i]
+// w_i -= sum_k h[p(i)][k] V_k[i], then (scal non-null) w_i *= scal[p(i)]
 __global__ void k_seg_maxpy(SegDev sg, int64_t n, int32_t nv, const double* __restrict__ V, int64_t ldv,
-                            const double* __restrict__ h, int32_t ldh, double* __restrict__ w, const int* guard) {
+                            const double* __restrict__ h, int32_t ldh, double* __restrict__ w,
+                            const double* __restrict__ scal, const int* guard) {
   if (off(guard)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double* hp = h + (int64_t)sg.node_prob[i / 7] * ldh;
+    const int p = sg.node_prob[i / 7];
+    const double* hp = h + (int64_t)p * ldh;
     double s = w[i];
     for (int k = 0; k < nv; ++k) s -= hp[k] * V[(int64_t)k * ldv + i];
-    w[i] = s;
+    w[i] = scal ? s * scal[p] : s;
   }
 }
 
@@ -116,6 +137,68 @@ __global__ void k_seg_scale_inv(SegDev sg, int64_t n, const double* __restrict__
       pc = p;
     }
     y[i] = x[i] * inv;
+  }
+}
+
+// Classical Gram-Schmidt twice with the new vector's norm taken from the second
+// pass: after w1 = w0 - V h1 the second pass's dots h2 = V^T w1 come with
+// ||w1||^2 (k_seg_mdot with the self product), and since V is orthonormal,
+// ||w1 - V h2||^2 = ||w1||^2 - ||h2||^2. The second update then scales in the
+// same sweep (k_seg_maxpy with scal), so the step needs no norm or scaling sweep.
+//
+// For every problem p, hb[p][0..j] = h2 and hb[p][j+1] = ||w1||^2: where
+// ||w1||^2 - ||h2||^2 keeps at least 3/4 of ||w1||^2 (the subtraction then loses
+// under two bits) H[p][j+1][j] (hsub + p * ldsub) is its square root and inv[p]
+// the reciprocal (0 for a zero norm); elsewhere (only as a Krylov space is
+// exhausted; for every problem with force = 1, tests of that path) inv[p] = 1,
+// unsafe[p] = 1 and *flag = 1: the norm is then formed from the updated vector
+// by the guarded k_seg_norm_fix path.
+__global__ void k_seg_norm_pythagoras(int32_t P, const double* __restrict__ hb, int32_t lda, int32_t j,
+                                      double* __restrict__ hsub, int64_t ldsub, double* __restrict__ inv,
+                                      int* __restrict__ unsafe, int* __restrict__ flag, int force,
+                                      const int* guard) {
+  __shared__ int s_any;
+  if (off(guard)) {
+    if (threadIdx.x == 0) *flag = 0;
+    return;
+  }
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const double* h = hb + (int64_t)p * lda;
+    const double s = h[j + 1];
+    double q = 0.0;
+    for (int k = 0; k <= j; ++k) q += h[k] * h[k];
+    const double b2 = s - q;
+    if (!force && b2 >= 0.75 * s) {
+      const double b = sqrt(b2);
+      hsub[(int64_t)p * ldsub] = b;
+      inv[p] = b > 0.0 ? 1.0 / b : 0.0;
+      unsafe[p] = 0;
+    } else {
+      inv[p] = 1.0;
+      unsafe[p] = 1;
+      atomicOr(&s_any, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = s_any;
+}
+
+// the fallback of k_seg_norm_pythagoras, after nrm[p] = ||w_p|| of the updated
+// vector: H[p][j+1][j] = nrm[p] and scal[p] = nrm[p] where unsafe[p], scal[p] = 1
+// elsewhere (the vector is then divided by scal)
+__global__ void k_seg_norm_fix(int32_t P, const double* __restrict__ nrm, const int* __restrict__ unsafe,
+                               double* __restrict__ hsub, int64_t ldsub, double* __restrict__ scal,
+                               const int* guard) {
+  if (off(guard)) return;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    if (unsafe[p]) {
+      hsub[(int64_t)p * ldsub] = nrm[p];
+      scal[p] = nrm[p];
+    } else {
+      scal[p] = 1.0;
+    }
   }
 }
 
@@ -295,8 +378,18 @@ void launch_seg_reorth_decide(int32_t P, const double* ws, const double* nrm, in
 }
 
 void launch_seg_maxpy(const SegDev& sg, int64_t n, int32_t nv, const double* V, int64_t ldv, const double* h,
-                      int32_t ldh, double* w, const int* guard, cudaStream_t s) {
-  k_seg_maxpy<<<grid_for(n, 256), 256, 0, s>>>(sg, n, nv, V, ldv, h, ldh, w, guard);
+                      int32_t ldh, double* w, const int* guard, cudaStream_t s, const double* scal) {
+  k_seg_maxpy<<<grid_for(n, 256), 256, 0, s>>>(sg, n, nv, V, ldv, h, ldh, w, scal, guard);
+}
+
+void launch_seg_norm_pythagoras(int32_t P, const double* hb, int32_t lda, int32_t j, double* hsub, int64_t ldsub,
+                                double* inv, int* unsafe, int* flag, int force, const int* guard, cudaStream_t s) {
+  k_seg_norm_pythagoras<<<1, 256, 0, s>>>(P, hb, lda, j, hsub, ldsub, inv, unsafe, flag, force, guard);
+}
+
+void launch_seg_norm_fix(int32_t P, const double* nrm, const int* unsafe, double* hsub, int64_t ldsub, double* scal,
+                         const int* guard, cudaStream_t s) {
+  k_seg_norm_fix<<<1, 256, 0, s>>>(P, nrm, unsafe, hsub, ldsub, scal, guard);
 }
 
 void launch_seg_scale_inv(const SegDev& sg, int64_t n, const double* x, const double* scal, int32_t lds,

@@ -269,3 +269,66 @@ def test_chunked_jacobian_assembly_is_bitwise_identical(tube0, precision):
         mats.append(fsi.fsi_jacobian_export(S.ctx)[2])
         S.close()
     assert np.array_equal(mats[0], mats[1]) and np.array_equal(mats[0], mats[2])
+
+
+# ---------------------------------------------------------------------------
+# Gram-Schmidt forms
+# ---------------------------------------------------------------------------
+def _solve_fp64_operator(m, **opt):
+    """GMRES on the FP64 Jacobian (FP64 preconditioner) to a relative residual of
+    1e-10: reachable only if the Arnoldi relation holds to about that accuracy,
+    so it measures the orthogonalisation."""
+    y, y1, y2 = perturbed_states(m, 40)
+    P = oracle_problem(m)
+    b = P.residual(y, y1, y2, 0.25 + P.dt)
+    S = make_solver(m, n_subdomains=4, gmres_rtol=1e-10, gmres_maxit=600, **opt)
+    S.set_state(y1, y2, None, t=0.25)
+    S.jacobian(y)
+    x = S.vec()
+    st = fsi.fsi_linear_solve(S.ctx, S.vec(b), x)
+    S.close()
+    return st, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("fault_test", [0, 2])
+def test_pythagorean_norm_gram_schmidt_matches_six_sweep_form(tube0, fault_test):
+    """orth = 0 takes the new Arnoldi vector's norm from the second pass,
+    sqrt(||w||^2 - ||h2||^2), and scales in the second update's sweep. On the
+    FP64 operator it reaches a 1e-10 relative residual in the iterations of the
+    six-sweep form (orth = 2) and the direct solve's solution; fault_test = 2
+    forms every norm from the updated vector instead (the fallback path)."""
+    import scipy.sparse.linalg as spla
+    m = tube0
+    st2, x2 = _solve_fp64_operator(m, orth=2)
+    st0, x0 = _solve_fp64_operator(m, orth=0, fault_test=fault_test)
+    for st in (st2, st0):
+        assert st.converged == 1 and st.rnorm <= 1e-10 * st.rnorm0 * 1.0001
+    assert abs(st0.iterations - st2.iterations) <= 1, (st2.iterations, st0.iterations)
+    y, y1, y2 = perturbed_states(m, 40)
+    P = oracle_problem(m)
+    Jo = P.jacobian(y, y1, y2, 0.25 + P.dt)
+    b = P.residual(y, y1, y2, 0.25 + P.dt)
+    xo = spla.spsolve(Jo.tocsc(), b.reshape(-1)).reshape(-1, 7)
+    for x in (x0, x2):
+        rel = rel_by_group(x, xo)
+        assert all(v < 1e-6 for v in rel.values()), rel
+
+
+def test_orth_option_range(tube0):
+    with pytest.raises(fsi.FsiError):
+        make_solver(tube0, orth=3, n_subdomains=4)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-6)])
+def test_newton_steps_with_six_sweep_gram_schmidt_match_oracle(tube0, oracle_tube0_steps, precision, tol):
+    """The six-sweep form (orth = 2) gives the oracle's Newton steps too."""
+    y0, ref = oracle_tube0_steps
+    S = make_solver(tube0, precision=precision, newton_rtol=1e-10, gmres_rtol=1e-6 if precision == 0 else 1e-4,
+                    n_subdomains=4, orth=2)
+    S.set_state(y0, t=0.0)
+    for k in range(5):
+        st = S.step()
+        y, _ = S.state()
+        rel = rel_by_group(y, ref[k])
+        assert st.converged == 1
+        assert all(v < tol for v in rel.values()), (k, rel)
