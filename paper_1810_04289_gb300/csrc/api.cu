@@ -351,21 +351,22 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
   const int64_t n = c->n;
   const int32_t m = c->m, ldh = m + 1, P = c->nprob;
   double* w = c->V + (int64_t)(j + 1) * n;
+  int nk = 0;  // multi-dot kernels launched (one or two per call)
   if (c->opt.orth == 1) {
     // classical Gram-Schmidt with a second pass only where the first removed more
     // than 1 - 1/sqrt(2) of ||w|| (the pass-2 kernels are guarded by that test)
     double* hj = c->H + (int64_t)j * ldh + j + 1;
-    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st, 1);
+    nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st, 1);
     launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
     launch_seg_norm(c->seg, w, c->partial, hj, ldh * m, guard, st);
     launch_seg_reorth_decide(P, c->hA + j + 1, hj, ldh * m, c->hB, ldh, j, c->active, c->reorth, st);
-    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, c->reorth, st);
+    nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, c->reorth, st);
     launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, c->reorth, st);
     launch_seg_norm(c->seg, w, c->partial, hj, ldh * m, c->reorth, st);
     launch_seg_scale_inv(c->seg, n, w, hj, ldh * m, w, guard, st);
     launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
                       c->kcols, c->anyact, st);
-    c->launches += 9;
+    c->launches += 7 + nk;
     return;
   }
   if (c->opt.orth == 0) {
@@ -374,9 +375,9 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
     // in one sweep. Where that norm is unsafe the guarded kernels form it from the
     // updated vector.
     double* hj = c->H + (int64_t)j * ldh + j + 1;
-    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
+    nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
     launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
-    launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st, 1);
+    nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st, 1);
     launch_seg_norm_pythagoras(P, c->hB, ldh, j, hj, (int64_t)ldh * m, c->gs_inv, c->gs_unsafe, c->reorth,
                                c->opt.fault_test == 2 ? 1 : 0, guard, st);
     launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, guard, st, c->gs_inv);
@@ -385,20 +386,20 @@ void arnoldi_step(fsi_ctx* c, int32_t j, const int* guard, cudaStream_t st) {
     launch_seg_scale_inv(c->seg, n, w, c->gs_scal, 1, w, c->reorth, st);
     launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
                       c->kcols, c->anyact, st);
-    c->launches += 9;
+    c->launches += 7 + nk;
     return;
   }
   // orth 2: dots, update, dots, update, norm, scale
-  launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
+  nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hA, ldh, guard, st);
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hA, ldh, w, guard, st);
-  launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
+  nk += launch_seg_mdot(c->seg, j + 1, c->V, n, w, c->partial, c->hB, ldh, guard, st);
   launch_seg_maxpy(c->seg, n, j + 1, c->V, n, c->hB, ldh, w, guard, st);
   // H[p][j+1][j] = ||w_p||, written in place (per-problem stride ldh * m), then w_p /= it
   launch_seg_norm(c->seg, w, c->partial, c->H + (int64_t)j * ldh + j + 1, ldh * m, guard, st);
   launch_seg_scale_inv(c->seg, n, w, c->H + (int64_t)j * ldh + j + 1, ldh * m, w, guard, st);
   launch_seg_givens(P, c->hA, c->hB, ldh, c->H, ldh, m, j, c->cs, c->sn, c->g, c->gres, c->gtarget, c->active,
                     c->kcols, c->anyact, st);
-  c->launches += 6;
+  c->launches += 5 + nk;
 }
 
 // The kernels of one restart cycle for every problem, from V_0 = r / ||r|| to

@@ -156,9 +156,10 @@ struct SegDev {
   int* counter;              // [P * SEG_GROUPS] blocks done per (problem, vector group); zero between launches
 };
 constexpr int SEG_GROUPS = 9;  // vector groups of 8 in one multi-dot (restart <= 64 -> at most 65 vectors)
-// out[p * ldo + k] = V_k . w for k < nv (and, with_self, out[p * ldo + nv] = w . w)
-void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                     double* out, int32_t ldo, const int* guard, cudaStream_t s, int with_self = 0);
+// out[p * ldo + k] = V_k . w for k < nv (and, with_self, out[p * ldo + nv] = w . w);
+// returns the number of kernels launched (1 or 2)
+int launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
+                    double* out, int32_t ldo, const int* guard, cudaStream_t s, int with_self = 0);
 // selective reorthogonalisation test after one Gram-Schmidt pass (see krylov.cu)
 void launch_seg_reorth_decide(int32_t P, const double* ws, const double* nrm, int32_t ldn, double* hb, int32_t lda,
                               int32_t j, const int* active, int* flag, cudaStream_t s);

@@ -32,57 +32,60 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // out[p * ldo + k] = sum over the dofs of problem p of V_k . w (V null: w . w,
 // and take_sqrt gives the 2-norm). Block (c, y) forms the partials of chunk c
-// for vectors 8y .. 8y+7; the last block of problem p for group y sums the
-// problem's partials (one warp per vector, lanes over the chunks in fixed order)
-// and resets the counter.
+// for the vectors of group g = g0 + y, 8g .. 8g + W - 1 (those below nv); the
+// last block of problem p for group g sums the problem's partials (one warp per
+// vector, lanes over the chunks in fixed order) and resets the counter.
 // With nself = 1 there is one more output, index nv_v = nv - 1: w . w itself.
-__global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const double* __restrict__ V, int64_t ldv,
-                                                 const double* __restrict__ w, double* __restrict__ partial,
-                                                 double* __restrict__ out, int32_t ldo, int take_sqrt,
-                                                 int nself, const int* guard) {
+// Each thread takes U elements per trip (loads in flight); the kernel is bound by
+// the FP64 pipe (one FMA per loaded operand) or, for narrow groups, by latency,
+// so the full groups run with W = 8, U = 2 and a partial last group in its own
+// launch with a narrower W and a deeper U (fewer registers, more loads in flight).
+template <int W, int U>
+__global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, int32_t g0, const double* __restrict__ V,
+                                                 int64_t ldv, const double* __restrict__ w,
+                                                 double* __restrict__ partial, double* __restrict__ out,
+                                                 int32_t ldo, int take_sqrt, int nself, const int* guard) {
   if (off(guard)) return;
-  __shared__ double red[MD][RB / 32];
+  __shared__ double red[W][RB / 32];
   __shared__ int s_last;
   const int c = blockIdx.x;
-  const int k0 = blockIdx.y * MD;
+  const int g = g0 + blockIdx.y;
+  const int k0 = g * MD;
   const int64_t i0 = sg.chunk_beg[c], i1 = sg.chunk_beg[c + 1];
-  double acc[MD];
+  double acc[W];
 #pragma unroll
-  for (int k = 0; k < MD; ++k) acc[k] = 0.0;
+  for (int k = 0; k < W; ++k) acc[k] = 0.0;
   const int nvv = nv - nself;  // vectors of V; the rest is w itself
   // vector k of this group: V_{k0+k} while k0 + k < nvv, else w (the self product)
-  const double* src[MD];
+  const double* src[W];
 #pragma unroll
-  for (int k = 0; k < MD; ++k) src[k] = (V && k0 + k < nvv) ? V + (int64_t)(k0 + k) * ldv : w;
-  // two elements per trip (the second predicated on the chunk's end): twice the
-  // loads in flight per thread. The kernel is bound by the FP64 pipe (one FMA per
-  // loaded operand), so only the group's live vectors take FMAs.
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += 2 * RB) {
-    const int64_t i2 = i + RB;
-    const bool two = i2 < i1;
-    const double wa = w[i], wb = two ? w[i2] : 0.0;
-    double va[MD], vb[MD];
+  for (int k = 0; k < W; ++k) src[k] = (V && k0 + k < nvv) ? V + (int64_t)(k0 + k) * ldv : w;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += U * RB) {
+    double wv[U], v[U][W];
 #pragma unroll
-    for (int k = 0; k < MD; ++k) {
-      va[k] = k0 + k < nv ? src[k][i] : 0.0;
-      vb[k] = (k0 + k < nv && two) ? src[k][i2] : 0.0;
+    for (int u = 0; u < U; ++u) {
+      const int64_t iu = i + u * RB;
+      const bool in = iu < i1;
+      wv[u] = in ? w[iu] : 0.0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) v[u][k] = (k0 + k < nv && in) ? src[k][iu] : 0.0;
     }
 #pragma unroll
-    for (int k = 0; k < MD; ++k) {
-      if (k0 + k < nv) {
-        acc[k] += va[k] * wa;
-        acc[k] += vb[k] * wb;
-      }
-    }
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        if (k0 + k < nv) acc[k] += v[u][k] * wv[u];
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < MD; ++k) {
-    double v = warp_sum(acc[k]);
-    if (lane == 0) red[k][warp] = v;
+  for (int k = 0; k < W; ++k) {
+    if (k0 + k < nv) {
+      const double v = warp_sum(acc[k]);
+      if (lane == 0) red[k][warp] = v;
+    }
   }
   __syncthreads();
-  if (threadIdx.x < MD && k0 + threadIdx.x < nv) {
+  if (threadIdx.x < W && k0 + threadIdx.x < nv) {
     double v = 0.0;
     for (int q = 0; q < RB / 32; ++q) v += red[threadIdx.x][q];
     partial[(int64_t)c * nv + k0 + threadIdx.x] = v;
@@ -92,13 +95,13 @@ __global__ void __launch_bounds__(RB) k_seg_mdot(SegDev sg, int32_t nv, const do
   __syncthreads();
   const int p = sg.node_prob[i0 / 7];
   const int64_t c0 = sg.prob_chunk[p], c1 = sg.prob_chunk[p + 1];
-  int* cnt = sg.counter + (int64_t)p * SEG_GROUPS + blockIdx.y;
+  int* cnt = sg.counter + (int64_t)p * SEG_GROUPS + g;
   if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1) == (int)(c1 - c0) - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   const int k = k0 + warp;
-  if (warp < MD && k < nv) {
+  if (warp < W && k < nv) {
     double v = 0.0;
     for (int64_t cc = c0 + lane; cc < c1; cc += 32) v += __ldcg(partial + cc * nv + k);
     v = warp_sum(v);
@@ -357,20 +360,40 @@ inline int grid_for(int64_t work, int block) {
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+// groups of 8 vectors in one launch, then the partial last group (r vectors) in a
+// launch of its own width
+void mdot_groups(const SegDev& sg, int32_t n, const double* V, int64_t ldv, const double* w, double* partial,
+                 double* out, int32_t ldo, int take_sqrt, int nself, const int* guard, cudaStream_t s) {
+  const unsigned nch = (unsigned)sg.n_chunks;
+  const int full = n / MD, r = n % MD;
+  if (full > 0)
+    k_seg_mdot<8, 2><<<dim3(nch, full), RB, 0, s>>>(sg, n, 0, V, ldv, w, partial, out, ldo, take_sqrt, nself, guard);
+  if (r == 0) return;
+  const dim3 g1(nch, 1);
+  if (r == 1)
+    k_seg_mdot<1, 8><<<g1, RB, 0, s>>>(sg, n, full, V, ldv, w, partial, out, ldo, take_sqrt, nself, guard);
+  else if (r == 2)
+    k_seg_mdot<2, 4><<<g1, RB, 0, s>>>(sg, n, full, V, ldv, w, partial, out, ldo, take_sqrt, nself, guard);
+  else if (r <= 4)
+    k_seg_mdot<4, 4><<<g1, RB, 0, s>>>(sg, n, full, V, ldv, w, partial, out, ldo, take_sqrt, nself, guard);
+  else
+    k_seg_mdot<8, 2><<<g1, RB, 0, s>>>(sg, n, full, V, ldv, w, partial, out, ldo, take_sqrt, nself, guard);
+}
+
 }  // namespace
 
-void launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
-                     double* out, int32_t ldo, const int* guard, cudaStream_t s, int with_self) {
+int launch_seg_mdot(const SegDev& sg, int32_t nv, const double* V, int64_t ldv, const double* w, double* partial,
+                    double* out, int32_t ldo, const int* guard, cudaStream_t s, int with_self) {
   const int n = nv + (with_self ? 1 : 0);
-  dim3 grid((unsigned)sg.n_chunks, (n + MD - 1) / MD);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, n, V, ldv, w, partial, out, ldo, 0, with_self ? 1 : 0, guard);
+  mdot_groups(sg, n, V, ldv, w, partial, out, ldo, 0, with_self ? 1 : 0, guard, s);
+  return (n / MD > 0 ? 1 : 0) + (n % MD > 0 ? 1 : 0);
 }
 
 void launch_seg_norm(const SegDev& sg, const double* x, double* partial, double* out, int32_t ldo,
                      const int* guard, cudaStream_t s) {
-  dim3 grid((unsigned)sg.n_chunks, 1);
-  k_seg_mdot<<<grid, RB, 0, s>>>(sg, 1, nullptr, 0, x, partial, out, ldo, 1, 0, guard);
+  mdot_groups(sg, 1, nullptr, 0, x, partial, out, ldo, 1, 0, guard, s);
 }
+
 
 void launch_seg_reorth_decide(int32_t P, const double* ws, const double* nrm, int32_t ldn, double* hb, int32_t lda,
                               int32_t j, const int* active, int* flag, cudaStream_t s) {
