@@ -36,7 +36,7 @@ WORKLOADS = {
     "tube-160x48x22": dict(name="tube-160x48x22", kind="tube"),
     "tree-3gen": dict(name="tree-3gen", kind="tree"),
     "tree-3gen-h08": dict(name="tree-3gen", kind="tree", over=dict(h=0.08)),
-    "tree-7gen": dict(name="tree-7gen", kind="tree"),
+    "tree-7gen": dict(name="tree-7gen", kind="tree", dt=2e-3),  # the 7-generation tree is stepped at 2 ms
     "batch-64-tubes": dict(name="batch-64-tubes", kind="batch"),
 }
 MATERIAL = dict(rho_f=1.05, mu_f=0.035, rho_s=1.2, E_s=3.0e6, nu_s=0.45, eta_s=0.0)
@@ -72,6 +72,11 @@ TUNED = {
                                      jac_lag=3),
     ("tube-96x32x15", "fp64"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                     jac_lag=3),
+    # the 64-tube batch (3.67 M unknowns): the autotuner's choice for the mixed form
+    ("batch-64-tubes", "mixed"): dict(n_subdomains=1024, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
+                                      jac_lag=3),
+    ("batch-64-tubes", "fp64"): dict(n_subdomains=1024, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
+                                     jac_lag=3),
 }
 # DRAM bytes per launch (read + write) from one ncu capture of the kernel as it is
 # now, keyed by (workload, phase, precision, subdomains, ILU level, ordering);
@@ -95,6 +100,10 @@ def parse():
     p.add_argument("--jac-lag", type=int, default=None)
     p.add_argument("--orth", type=int, default=None,
                    help="Gram-Schmidt form (fsi_options.orth); default the library's (0)")
+    p.add_argument("--stages", type=int, default=None,
+                   help="streamed apply: ring stages (fsi_options.stages); default the library's choice")
+    p.add_argument("--stage-blocks", type=int, default=None,
+                   help="streamed apply: blocks per ring stage (fsi_options.stage_blocks)")
     p.add_argument("--newton-rtol", type=float, default=1e-6)
     p.add_argument("--gmres-rtol", type=float, default=1e-3)
     p.add_argument("--precisions", default="mixed,fp64")
@@ -238,11 +247,12 @@ def options_for(args, prec, fsi):
     base = dict(n_subdomains=256, overlap=1, ilu_level=1, ordering=1, threads_per_row=32, jac_lag=1)
     base.update(TUNED.get((args.workload, prec), {}))
     for k, a in (("n_subdomains", args.subdomains), ("ilu_level", args.ilu), ("overlap", args.overlap),
-                 ("ordering", args.ordering), ("jac_lag", args.jac_lag), ("orth", args.orth)):
+                 ("ordering", args.ordering), ("jac_lag", args.jac_lag), ("orth", args.orth),
+                 ("stages", args.stages), ("stage_blocks", args.stage_blocks)):
         if a is not None:
             base[k] = a
     return fsi.fsi_default_options(newton_rtol=args.newton_rtol, gmres_rtol=args.gmres_rtol, precision=pflag,
-                                   **base), (args.workload, prec) in TUNED
+                                   dt=WORKLOADS[args.workload].get("dt", 1e-3), **base), (args.workload, prec) in TUNED
 
 
 def run_ours(args, rank, world):
@@ -574,6 +584,7 @@ def main():
                    "options": "committed tuned choice" if head["committed"] and not args.autotune else
                    ("autotuned in this run" if args.autotune else "defaults / flags"),
                    "newton_rtol": args.newton_rtol, "gmres_rtol": args.gmres_rtol,
+                   "dt": WORKLOADS[args.workload].get("dt", 1e-3),
                    "l2": "working set (BSR + ILU factors) larger than L2 each step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "NI": ni, "LI_per_newton": float(np.mean([s["linear_iterations"] / max(1, s["newton_iterations"])

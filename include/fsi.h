@@ -150,7 +150,7 @@ typedef struct {
   int32_t stage_blocks;   /* streamed apply: factor blocks per ring stage, 0 = automatic
                              (sized so that every subdomain's CTA is resident) */
   int32_t stages;         /* streamed apply: ring stages in flight per warp, 2..8,
-                             0 = automatic (3) */
+                             0 = automatic (2) */
   int32_t orth;           /* Arnoldi orthogonalisation, FP64 (Sec. 4: classical
                              Gram-Schmidt twice): 0 the new vector's norm taken from the
                              second pass (dots; update; dots with ||w||^2; update and

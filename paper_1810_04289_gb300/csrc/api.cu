@@ -1002,7 +1002,7 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       // shared memory per CTA leaves after the vector; the stage_blocks and
       // stages options override the choice
       const int vsz = cp->mixed ? 4 : 8, stride = 56;  // packed block: 7 rows of 8 values
-      int nst = o.stages > 0 ? o.stages : 3;
+      int nst = o.stages > 0 ? o.stages : 2;
       const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
       const int64_t per_sm = std::min<int64_t>(8, (R.np + 151) / 152);
       const int64_t fixed = 128 * ((W * 64 + 127) / 128) + 8 * R.max_rows * vsz + 4 * R.max_rows + 16 + 1024;
