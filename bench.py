@@ -63,19 +63,21 @@ TUNED = {
                                  jac_lag=3),
     ("tree-7gen", "fp64"): dict(n_subdomains=49152, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                 jac_lag=3),
-    # the same tree at h = 0.08 (2.09 M unknowns): subdomains of the same size
-    ("tree-3gen-h08", "mixed"): dict(n_subdomains=2048, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+    # the same tree at h = 0.08 (2.09 M unknowns): subdomains of the same size;
+    # ILU(1) stagnates there (GMRES makes no progress in 1,000 iterations)
+    ("tree-3gen-h08", "mixed"): dict(n_subdomains=2048, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
                                      jac_lag=3),
-    ("tree-3gen-h08", "fp64"): dict(n_subdomains=2048, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
+    ("tree-3gen-h08", "fp64"): dict(n_subdomains=2048, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
                                     jac_lag=3),
     ("tube-96x32x15", "mixed"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                      jac_lag=3),
     ("tube-96x32x15", "fp64"): dict(n_subdomains=512, overlap=1, ilu_level=1, ordering=1, threads_per_row=32,
                                     jac_lag=3),
     # the 64-tube batch (3.67 M unknowns): the autotuner's choice for the mixed form
-    ("batch-64-tubes", "mixed"): dict(n_subdomains=1024, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
+    # (ILU(1) does not converge in 1,000 GMRES iterations at any subdomain count)
+    ("batch-64-tubes", "mixed"): dict(n_subdomains=8192, overlap=1, ilu_level=2, ordering=1, threads_per_row=16,
                                       jac_lag=3),
-    ("batch-64-tubes", "fp64"): dict(n_subdomains=1024, overlap=1, ilu_level=2, ordering=1, threads_per_row=32,
+    ("batch-64-tubes", "fp64"): dict(n_subdomains=8192, overlap=1, ilu_level=2, ordering=1, threads_per_row=16,
                                      jac_lag=3),
 }
 # DRAM bytes per launch (read + write) from one ncu capture of the kernel as it is
@@ -100,6 +102,8 @@ def parse():
     p.add_argument("--jac-lag", type=int, default=None)
     p.add_argument("--orth", type=int, default=None,
                    help="Gram-Schmidt form (fsi_options.orth); default the library's (0)")
+    p.add_argument("--threads-per-row", type=int, default=None, choices=[16, 32],
+                   help="BSR SpMV threads per block row (fsi_options.threads_per_row)")
     p.add_argument("--stages", type=int, default=None,
                    help="streamed apply: ring stages (fsi_options.stages); default the library's choice")
     p.add_argument("--stage-blocks", type=int, default=None,
@@ -248,7 +252,8 @@ def options_for(args, prec, fsi):
     base.update(TUNED.get((args.workload, prec), {}))
     for k, a in (("n_subdomains", args.subdomains), ("ilu_level", args.ilu), ("overlap", args.overlap),
                  ("ordering", args.ordering), ("jac_lag", args.jac_lag), ("orth", args.orth),
-                 ("stages", args.stages), ("stage_blocks", args.stage_blocks)):
+                 ("stages", args.stages), ("stage_blocks", args.stage_blocks),
+                 ("threads_per_row", args.threads_per_row)):
         if a is not None:
             base[k] = a
     return fsi.fsi_default_options(newton_rtol=args.newton_rtol, gmres_rtol=args.gmres_rtol, precision=pflag,

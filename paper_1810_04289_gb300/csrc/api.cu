@@ -1192,11 +1192,15 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
       return true;
     };
     int32_t it = 0;
+    int32_t jac_it = -1;  // iteration whose iterate the current Jacobian was evaluated at
+    bool refresh = false;  // a line search failed on a lagged Jacobian: evaluate it again here
     while (!all_done()) {
       if (it >= c->opt.newton_maxit) throw StatusError{FSI_ERR_DIVERGED, "Newton reached its iteration limit"};
-      if (it % c->opt.jac_lag == 0) {
+      if (jac_it < 0 || it - jac_it >= c->opt.jac_lag || refresh) {
         jacobian(c, c->yk);
         S.jacobian_evaluations++;
+        jac_it = it;
+        refresh = false;
       }
       CK(cudaMemcpyAsync(c->pmask, conv.data(), sizeof(int) * P, cudaMemcpyHostToDevice, c->s));
       c->launches += 1;
@@ -1213,8 +1217,8 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
         alpha[p] = conv[p] ? 0.0 : 1.0;
         pend[p] = !conv[p];
       }
-      bool any_pending = true;
-      while (any_pending) {
+      bool any_pending = true, retry = false;
+      while (any_pending && !retry) {
         CK(cudaMemcpyAsync(c->palpha, alpha.data(), sizeof(double) * P, cudaMemcpyHostToDevice, c->s));
         c->launches += 1;
         launch_seg_axpy(c->seg, n, c->yk, c->palpha, c->dy, c->ytr, c->s);
@@ -1236,10 +1240,20 @@ fsi_status fsi_step(fsi_ctx* c, fsi_step_stats* stats) {
               pend[p] = 0;
               continue;
             }
+            // a direction from a Jacobian of an earlier iterate (Jacobian lag) may
+            // not descend: evaluate the Jacobian here and redo this iteration once
+            if (jac_it != it) {
+              retry = true;
+              break;
+            }
             throw StatusError{FSI_ERR_LINESEARCH, "backtracking line search found no sufficient decrease"};
           }
           any_pending = true;
         }
+      }
+      if (retry) {
+        refresh = true;
+        continue;
       }
       std::swap(c->yk, c->ytr);
       std::swap(c->F, c->Ft);
