@@ -4,7 +4,8 @@
 // block per chunk, and the last block of a problem to finish (a per-problem
 // counter) sums that problem's chunk partials in fixed order, so results are
 // bitwise reproducible run to run, independent problems never mix, and a
-// reduction is one launch.
+// reduction is one launch per group width (a multi-dot: one for its full groups
+// of 8 vectors, one for a partial last group).
 // Per-problem Arnoldi scalars: H (column-major (m+1) x m per problem), g, Givens
 // cs/sn, residual estimates, stop flags.
 //
