@@ -150,6 +150,8 @@ struct WarpFeed {
   int seg;           // producer: current segment 0 .. 2D+1 (2D+2 = done)
   int pos, end;      // producer: next block to issue and end block of the current segment
   int issued, used;  // stages issued / consumed by this warp
+  int islot;         // producer: ring slot of the next issue (issued mod NST)
+  int uslot, uphase; // consumer: ring slot of the next stage (used mod NST) and its mbarrier phase parity
 };
 
 // item of segment j for warp wi, or -1 when the warp has no item in that phase
@@ -182,12 +184,13 @@ __device__ __forceinline__ void feed_issue(WarpFeed& f, const int32_t* ib, const
   feed_seek(f, ib);
   if (f.pos >= f.end) return;
   const int nb = min(SB, f.end - f.pos);
-  const int st = f.issued % NST;
+  const int st = f.islot;
   const uint32_t bytes = (uint32_t)(nb * STR * sizeof(TF));
   mbar_arrive_expect_tx(&full[st], bytes);
   bulk_g2s(ring + (size_t)st * SB * STR, (f.seg <= f.D ? Lpack : Upack) + (size_t)f.pos * STR, bytes, &full[st]);
   f.pos += nb;
   f.issued++;
+  if (++f.islot == NST) f.islot = 0;
 }
 
 // Multi-warp streamed RAS apply (Sec. 3, Eq. 16) on nested-dissection ordered
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   }
   __syncthreads();
 
-  WarpFeed f{D, wi, -1, 0, 0, 0, 0};
+  WarpFeed f{D, wi, -1, 0, 0, 0, 0, 0, 0, 0};
   const bool active = wi < (1 << D);
   if (active && lane == 0 && !R.stall)
     for (int k = 0; k < NST; ++k) feed_issue<TF, STR>(f, ib, Lpack, Upack, ring, full, NST, SB);
@@ -254,14 +257,18 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
   bool ok = true;
   // wait for the next stage of this warp's sequence; false on timeout
   auto next_stage = [&]() -> const TF* {
-    const int st = f.used % NST;
-    if (!mbar_wait(&full[st], (f.used / NST) & 1)) return nullptr;
+    const int st = f.uslot;
+    if (!mbar_wait(&full[st], (uint32_t)f.uphase)) return nullptr;
     return ring + (size_t)st * SB * STR;
   };
   // the stage is consumed: lane 0 refills its slot with the next stage in line
   auto release = [&]() {
     __syncwarp();
     f.used++;
+    if (++f.uslot == NST) {
+      f.uslot = 0;
+      f.uphase ^= 1;
+    }
     if (lane == 0 && !R.stall) feed_issue<TF, STR>(f, ib, Lpack, Upack, ring, full, NST, SB);
     f.issued = __shfl_sync(0xffffffffu, f.issued, 0);
   };
