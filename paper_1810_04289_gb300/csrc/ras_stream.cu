@@ -110,27 +110,26 @@ __device__ __forceinline__ double row7(const double* a, const double* x) {
 
 constexpr int NSTMAX = 8;  // most ring stages (runtime count R.nst)
 
-// sum over blocks b in [b0, nb) of (block b, row c) . w[col(b)], reduced over
-// the warp: lane = 7 j + c handles blocks b0 + j, b0 + j + 4, ...; every block
+// sum over blocks b in [0, nb) of (block b, row c) . w[col(b)], reduced over
+// the warp: lane = 7 j + c handles blocks j, j + 4, ...; every block
 // gathers its column index first so that all loads of a chunk are independent,
 // then forms the 7-term products (16-byte loads of the block row and of the
 // 8-wide node vector). The total lands in lanes 0..6.
 template <class TF, int STR>
-__device__ __forceinline__ TF row_dot(const TF* stg, int b0, int nb, const TF* w, int j, int c) {
+__device__ __forceinline__ TF row_dot(const TF* stg, int nb, const TF* w, int j, int c) {
   TF acc = TF(0);
   if (j < 4) {
-    for (int b = b0 + j; b < nb; b += 16) {
+    // 32-bit element offsets within the stage (a stage fits in shared memory)
+    for (int b = j; b < nb; b += 16) {
       int cols[4];
-      const TF* blk[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int bi = b + 4 * i;
-        blk[i] = stg + (size_t)(bi < nb ? bi : b) * STR;
-        cols[i] = bi < nb ? blk_col(blk[i]) : -1;
+        cols[i] = bi < nb ? blk_col(stg + bi * STR) : -1;
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (cols[i] >= 0) acc += row7(blk[i] + 8 * c, w + 8 * cols[i]);
+        if (cols[i] >= 0) acc += row7(stg + (b + 4 * i) * STR + 8 * c, w + 8 * cols[i]);
       }
     }
   }
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
         int pos = 0;
         if (rem > 0) {
           const int k = min(rem, cap);
-          acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+          acc += row_dot<TF, STR>(stg, k, w, j, c);
           pos = k;
           rem -= k;
           if (rem == 0) {
@@ -302,13 +301,13 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
           for (; q < qe; ++q) {
             const int nb = Lcnt[q];
             if (pos + nb > cap) break;
-            const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
+            const TF a = row_dot<TF, STR>(stg + pos * STR, nb, w, j, c);
             if (lane < 7 && nb > 0) w[8 * q + lane] -= a;
             __syncwarp();
             pos += nb;
           }
           if (q < qe && pos < cap) {
-            acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
+            acc = row_dot<TF, STR>(stg + pos * STR, cap - pos, w, j, c);
             rem = Lcnt[q] - (cap - pos);
           }
         }
@@ -337,7 +336,7 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
         int pos = 0;
         if (rem > 0) {
           const int k = min(rem, cap);
-          acc += row_dot<TF, STR>(stg, 0, k, w, j, c);
+          acc += row_dot<TF, STR>(stg, k, w, j, c);
           pos = k;
           rem -= k;
           if (rem == 0) {
@@ -350,13 +349,13 @@ __global__ void __launch_bounds__(256) k_ras_apply_stream(RasStreamDev R, const 
           for (; q >= qb; --q) {
             const int nb = Ucnt[q];
             if (pos + nb > cap) break;
-            const TF a = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, nb, w, j, c);
+            const TF a = row_dot<TF, STR>(stg + pos * STR, nb, w, j, c);
             if (lane < 7) w[8 * q + lane] = a;
             __syncwarp();
             pos += nb;
           }
           if (q >= qb && pos < cap) {
-            acc = row_dot<TF, STR>(stg + (size_t)pos * STR, 0, cap - pos, w, j, c);
+            acc = row_dot<TF, STR>(stg + pos * STR, cap - pos, w, j, c);
             rem = Ucnt[q] - (cap - pos);
           }
         }
