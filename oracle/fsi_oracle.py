@@ -31,6 +31,14 @@ Readings of points the paper leaves open (stabilisation form and constants,
 interface rows, boundary rows, line search) are listed in the module's design
 notes and restated next to the code that uses them.
 
+Parity unpinned: the values of the stabilisation parameters tau_M and tau_C. The
+paper defers the stabilisation to its references and fixes no constant; the pins
+check what the stabilised method must do with any admissible tau (patch tests,
+Poiseuille convergence, discrete mass conservation, dissipativity of the
+stabilisation terms, the complex-step Jacobian against finite differences), not
+the constants themselves. The interface rows are pinned (a pressurised coupled
+tube against the plane-strain Lame solution; wrong routings fail it).
+
 Node block layout (7 dofs): [u_x, u_y, u_z, p, d_x, d_y, d_z].
 """
 import numpy as np
