@@ -98,7 +98,7 @@ struct fsi_ctx {
   int* kcols = nullptr;          // [P] Krylov columns built in the cycle
   int* anyact = nullptr;         // [1] some problem active (guard of the captured kernels)
   int* reorth = nullptr;         // [1] some problem needs a second Gram-Schmidt pass (orth = 1), or
-                                 // the double-float Gram-Schmidt's norm from its updated vector
+                                 // its new norm from the updated vector (orth = 0 fallback)
   double* gs_inv = nullptr;      // [P] reciprocal of H[j+1][j] (orth 0)
   double* gs_nrm = nullptr;      // [P] norms formed from the updated vector (its fallback)
   double* gs_scal = nullptr;     // [P] their divisors
