@@ -148,7 +148,8 @@ typedef struct {
                              not fit); 2 level-scheduled. Same arithmetic, same result
                              up to the order of the row sums. */
   int32_t stage_blocks;   /* streamed apply: factor blocks per ring stage, 0 = automatic
-                             (sized so that every subdomain's CTA is resident) */
+                             (sized from the shared memory left at ceil(n_subdomains / 152),
+                             at most 8, CTAs per SM) */
   int32_t stages;         /* streamed apply: ring stages in flight per warp, 2..8,
                              0 = automatic (2) */
   int32_t orth;           /* Arnoldi orthogonalisation, FP64 (Sec. 4: classical

@@ -997,10 +997,10 @@ fsi_status fsi_create(const fsi_mesh* mesh, const fsi_material* mat, const fsi_b
       rs.Usrc = cp->upload(Usrc);
       rs.Ucol = cp->upload(Ucol);
       rs.Upiv = cp->upload(Upiv);
-      // stage geometry: NST stages of SB blocks. The subdomains should all be
-      // resident at once (ceil(np / 152) CTAs per SM), so the ring gets what the
-      // shared memory per CTA leaves after the vector; the stage_blocks and
-      // stages options override the choice
+      // stage geometry: NST (2) stages of SB blocks. The target is ceil(np / 152)
+      // CTAs per SM, at most 8 (all subdomains resident at once up to 1,216), and
+      // the ring gets what the shared memory per CTA leaves after the vector; the
+      // stage_blocks and stages options override the choice
       const int vsz = cp->mixed ? 4 : 8, stride = 56;  // packed block: 7 rows of 8 values
       int nst = o.stages > 0 ? o.stages : 2;
       const int64_t W = (int64_t)1 << R.max_depth;  // warps (rings) per CTA
